@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput of the Strang split step of the dimensionless 3D Gross-Pitaevskii equation.
+
+Workload (default): 256^3 periodic box, xi = 1.5 dx (alpha = sqrt(2) xi, beta = 2/alpha),
+dt = 0.002, random-vortex-ring initial condition (40 rings, radii in [4 xi, 12 xi], seed 0),
+float32 storage, fused sweeps.  A bench step is one time step of the scheme; the timed
+region is one gp_step call advancing K steps on a field already resident in HBM.
+
+Metric: N^3 * steps / s (grid points advanced per second), whole job.  Also reported:
+  roofline     the dominant sweep kernel: algorithmic bytes (16 B per point per launch,
+               one read and one write of the complex64 field) / its mean CUDA-event time,
+               against the measured HBM copy bandwidth; floor_frac = 32 N^3 B / (t_step * BW)
+               (two sweeps per step is the fewest a 3D FFT pair admits)
+  e2e          the same metric through gp_step_host with the field in pinned host memory,
+               one host->device copy, one step and one device->host copy per bench step
+  cpu_baseline the float64 numpy oracle, one full 256^3 step, on the host
+  fp64_plain   the unfused complex128 GPU path, cufft_torch the cuFFT + elementwise baseline
+  sizes        512^3 and 1024^3 (smoothed-random-phase start, k0 = 8, dt = 0.001)
+N > 1 GPUs (torchrun): every rank advances its own independent field (replicas; the
+ensemble shards without communication), value = all ranks' points * steps / max time.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_MAIN, DT_MAIN, RINGS = 256, 0.002, 40
+METRIC = "GP N^3*steps/s (fused FP32 split step)"
+UNIT = "N^3*steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gp", choices=["gp", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip fp64/cufft/large-size/cpu legs")
+    ap.add_argument("--sizes", default="512,1024")
+    ap.add_argument("--only-step", action="store_true", help="init, warm-up and the timed steps only (profiling)")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gp_fft.cuh", "gp_sweep.cuh"):
+        with open(os.path.join(ROOT, "paper_2003_03590_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, n):
+    """dram read+write bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (lines: <kernel> <n> <bytes_per_launch> <source_hash>)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = kernel_source_hash()
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) == 4 and not line.startswith("#") and parts[0] == kernel and int(parts[1]) == n \
+                    and parts[3] == cur:
+                return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.barrier()
+        torch.cuda.synchronize()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_plan(gq, n, dt, prec):
+    return gq.Plan(gq.field_params(n, dt, xi_over_dx=1.5, precision=prec))
+
+
+def init_rvr(gq, plan, seed):
+    a, b = plan.coefficients()
+    xi = math.sqrt(a / b)
+    return plan.init_rvr(0, plan.empty(), seed=seed, mode=0, count=RINGS, p0=4 * xi, p1=12 * xi)
+
+
+def time_steps(plan, psi, k):
+    import torch
+    s = plan.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    plan.step([psi], k)
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def roofline_of(gq, plan, psi, n, ksteps, peak):
+    gq.profile(plan, True)
+    plan.step([psi], ksteps)
+    rec = gq.profile_read(plan)
+    gq.profile(plan, False)
+    per_kernel = {}
+    for name, (cnt, ms) in rec.items():
+        kern = name.split(":")[0]
+        c, m = per_kernel.get(kern, (0, 0.0))
+        per_kernel[kern] = (c + cnt, m + ms)
+    total = sum(m for _, m in per_kernel.values())
+    kern, (cnt, ms) = max(per_kernel.items(), key=lambda kv: kv[1][1])
+    per_launch_s = ms / cnt / 1e3
+    alg_bytes = 16.0 * n ** 3
+    achieved = alg_bytes / per_launch_s / 1e9
+    traffic = ncu_traffic(kern, n)
+    return {"kernel": kern, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_bytes": alg_bytes,
+            "launches": cnt, "mean_launch_us": round(per_launch_s * 1e6, 2), "time_share": round(ms / total, 3),
+            "kernels": {k: {"launches": c, "ms": round(m, 3), "share": round(m / total, 3)}
+                        for k, (c, m) in per_kernel.items()},
+            "kinds_mean_us": {k: round(ms_ / c_ * 1e3, 2) for k, (c_, ms_) in rec.items()}}
+
+
+def cpu_oracle_baseline(n, dt, steps):
+    """The float64 oracle, as it stands, on the host: `steps` full steps of the n^3 workload."""
+    from inputs import random_psi
+    from oracle import scheme as OS
+    p = OS.params_from_dx_ratio(n, 1.5, dt)
+    # the step's cost does not depend on the values: a seeded field of the workload's size
+    psi = random_psi(n, 0, amp_jitter=0.1)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        psi = OS.step_nkn(psi, p)
+    dt_s = time.perf_counter() - t0
+    return n ** 3 * steps / dt_s, dt_s
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return 0
+    k = max(1, min(args.steps, 2))
+    w = min(args.warmup, 0)
+    val, secs = cpu_oracle_baseline(N_MAIN, DT_MAIN, k)
+    cores = 1
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": k, "warmup": w, "ms_per_step": secs * 1e3 / k, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"GP split step {N_MAIN}^3, xi=1.5dx, dt={DT_MAIN}, RVR {RINGS} rings",
+                       "global_batch": 1, "seq_len": N_MAIN ** 3, "parallelism": "single process, host"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{k} full float64 NKN step(s) of the {N_MAIN}^3 field (numpy oracle)"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import paper_2003_03590_gb300.gpqt as gq
+    world, rank, local = dist_setup()
+    peak, peak_src = peaks()
+    n, K, W = N_MAIN, args.steps, max(3, args.warmup)
+
+    plan = make_plan(gq, n, DT_MAIN, gq.GP_FP32)
+    psi = init_rvr(gq, plan, seed=rank)
+    plan.step([psi], W)                       # warm-up (also captures the step graph)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.2)
+    l0 = gq.launch_count(plan)
+    ms = time_steps(plan, psi, K)
+    launches = gq.launch_count(plan) - l0
+    clk = clocks.stop()
+    barrier(world)
+    ms = max_over_ranks(ms, world)
+    value = n ** 3 * K * world / (ms / 1e3)
+    if args.only_step:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "steps": K, "ms_per_step": ms / K}))
+        return 0
+    ms_step = ms / K
+    floor_frac = 32.0 * n ** 3 / (ms_step / 1e3) / (peak * 1e9)
+
+    roof = roofline_of(gq, plan, psi, n, min(K, 200), peak)
+    roof["floor_frac"] = round(floor_frac, 4)
+    roof["peak_source"] = peak_src
+    roof["sweeps_per_step"] = 4
+
+    # end to end through the public C ABI with host buffers
+    host = torch.empty((n, n, n), dtype=torch.complex64).pin_memory()
+    host.copy_(psi.cpu())
+    k_e2e = min(K, 50)
+    plan.step_host([host], 1)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        plan.step_host([host], 1)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e = {"value": n ** 3 * k_e2e * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * n ** 3,
+           "d2h_bytes_per_step": 8 * n ** 3, "steps": k_e2e,
+           "how": "gp_step_host(pinned host field, 1 step) per bench step: H2D copy, fused step, D2H copy"}
+    t0 = time.perf_counter()
+    plan.step_host([host], K)
+    run_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e["whole_run"] = {"value": n ** 3 * K * world / run_s, "steps": K,
+                        "how": "one gp_step_host call: one H2D, K steps, one D2H"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"GP split step {n}^3, xi=1.5dx, dt={DT_MAIN}, RVR {RINGS} rings, fused FP32",
+                       "global_batch": world, "seq_len": n ** 3, "parallelism": f"replicas x{world}",
+                       "l2": f"field {8 * n ** 3 / 1e6:.0f} MB > 129 MB L2; no flush between steps"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+
+    if not args.no_extras and rank == 0:
+        extras = {}
+        # plain float64 GPU path on the same workload
+        p64 = make_plan(gq, n, DT_MAIN, gq.GP_FP64)
+        psi64 = init_rvr(gq, p64, seed=0)
+        p64.step([psi64], 2)
+        k64 = 20
+        ms64 = time_steps(p64, psi64, k64)
+        extras["fp64_plain"] = {"value": n ** 3 * k64 / (ms64 / 1e3), "ms_per_step": ms64 / k64, "steps": k64}
+        del psi64, p64
+        # cuFFT + separate elementwise kernels (timed baseline only)
+        a, b = plan.coefficients()
+        kk = torch.fft.fftfreq(n, 1.0 / n, device="cuda", dtype=torch.float64)
+        k2 = kk[:, None, None] ** 2 + kk[None, :, None] ** 2 + kk[None, None, :] ** 2
+        ek = torch.polar(torch.ones_like(k2), -a * k2 * DT_MAIN).to(torch.complex64)
+        del k2
+        x = psi.clone()
+        h = 0.5 * DT_MAIN
+
+        def torch_step(x):
+            x = x * torch.polar(torch.ones_like(x.real), -b * h * (x.real ** 2 + x.imag ** 2 - 1))
+            x = torch.fft.ifftn(torch.fft.fftn(x) * ek)
+            return x * torch.polar(torch.ones_like(x.real), -b * h * (x.real ** 2 + x.imag ** 2 - 1))
+
+        for _ in range(3):
+            x = torch_step(x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kcu = 100
+        e0.record()
+        for _ in range(kcu):
+            x = torch_step(x)
+        e1.record()
+        torch.cuda.synchronize()
+        mcu = e0.elapsed_time(e1)
+        extras["cufft_torch"] = {"value": n ** 3 * kcu / (mcu / 1e3), "ms_per_step": mcu / kcu, "steps": kcu}
+        del x, ek
+        # larger grids
+        sizes = {}
+        for s in [int(v) for v in args.sizes.split(",") if v.strip()]:
+            ps = make_plan(gq, s, 0.001, gq.GP_FP32)
+            f = ps.init_srp(0, ps.empty(), seed=0, mode=0, p0=8.0, p1=math.pi)
+            ps.step([f], 5)
+            ks = 100 if s <= 512 else 40
+            mss = time_steps(ps, f, ks)
+            r = roofline_of(gq, ps, f, s, min(ks, 20), peak)
+            sizes[str(s)] = {"value": s ** 3 * ks / (mss / 1e3), "ms_per_step": mss / ks, "steps": ks,
+                             "floor_frac": round(32.0 * s ** 3 / (mss / ks / 1e3) / (peak * 1e9), 4),
+                             "dominant": {k: r[k] for k in ("kernel", "achieved", "frac", "time_share")}}
+            del f, ps
+            torch.cuda.empty_cache()
+        extras["sizes"] = sizes
+        # the float64 oracle on the host cores: one full step of the same 256^3 workload
+        val, secs = cpu_oracle_baseline(n, DT_MAIN, 1)
+        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"1 full float64 NKN step of the {n}^3 field ({secs:.1f} s, numpy)"}
+        line["extras"] = extras
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * gp.h -- C ABI of the GB300 Gross-Pitaevskii split-step library (libgpqt.so).
+ *
+ * Method: Kobayashi et al., "Quantum turbulence simulations using the
+ * Gross-Pitaevskii equation: HPC and new numerical benchmarks".
+ *   equation      i dpsi/dt = -alpha lap(psi) + beta (|psi|^2 - 1) psi    (Sec. 4.1, eq-gpe-num)
+ *   box           [0, 2 pi]^3, periodic, N points per axis, x_i = 2 pi i / N (Sec. 6)
+ *   parameters    alpha beta = 2 (M = 1/2), xi = sqrt(alpha/beta)           (Sec. 4.1, eq-scaling-choice3)
+ *   time step     Strang splitting into exact kinetic and nonlinear flows    (Sec. 4.3, eq:adi_looptime)
+ *
+ * Conventions shared by every entry point
+ *   - Fields are complex, interleaved (re, im), C order [z][y][x] (x fastest):
+ *     element (x, y, z) sits at index (z*N + y)*N + x.  GP_FP32 fields are
+ *     complex64 (8 bytes per point), GP_FP64 fields complex128 (16 bytes).
+ *   - Unless a name ends in _host, field pointers are DEVICE pointers owned by
+ *     the caller and must be 16-byte aligned; the library never frees them.
+ *   - The plan owns its tables, workspaces and captured CUDA graphs and frees
+ *     them in gp_plan_destroy.
+ *   - Work is enqueued on the plan's stream and is asynchronous unless the
+ *     entry point returns host values (then it synchronises that stream).
+ *   - Every call returns a gp_status and never aborts, exits or traps; the
+ *     message of the last failure is available from gp_last_error().
+ *   - Device-side problems (non-finite values found by a reduction, a bounded
+ *     wait that ran out) are reported at the next synchronising call.
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GP_OK = 0,
+  GP_ERR_INVALID_ARG = 1,      /* null pointer, misaligned pointer, bad index or value */
+  GP_ERR_UNSUPPORTED_SIZE = 2, /* N not one of the supported grid sizes */
+  GP_ERR_OOM = 3,              /* device allocation of a workspace failed */
+  GP_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+  GP_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
+  GP_ERR_NONFINITE = 6         /* a reduction met NaN or Inf */
+} gp_status;
+
+typedef enum { GP_FP32 = 0, GP_FP64 = 1 } gp_precision;
+/* GP_FP32: complex64 storage, fused sweeps (the nonlinear phase is applied
+ *          inside the FFT sweeps, the kinetic propagator inside the middle sweep).
+ * GP_FP64: complex128 storage, plain unfused path (one kernel per sub-flow and
+ *          per FFT axis), the accuracy reference on the GPU. */
+
+typedef enum { GP_SPLIT_NKN = 0, GP_SPLIT_KNK = 1 } gp_split;
+/* NKN: psi' = N(dt/2) K(dt) N(dt/2) psi, consecutive half steps merged.
+ * KNK: the paper's order (eq:adi_looptime), K(dt/2) N(dt) K(dt/2).
+ * K(s): psi_k <- exp(-i alpha |k|^2 s) psi_k in Fourier space (the product of
+ *       the three exact directional flows S(s, L_j), which commute).
+ * N(s): psi <- exp(-i beta (|psi|^2 - c) s) psi pointwise, c = 1 or 0. */
+
+typedef struct {
+  int n;                 /* grid points per axis: 8 12 16 24 32 48 64 96 128 192 256 512 1024 */
+  double xi;             /* healing length; used when alpha == 0 and beta == 0 */
+  double alpha, beta;    /* 0, 0 => alpha = sqrt(2) xi, beta = 2 / alpha */
+  double dt;             /* time step (finite; may be negative for time reversal) */
+  int precision;         /* gp_precision */
+  int split;             /* gp_split */
+  int nonlin_minus_one;  /* 1: phase beta (|psi|^2 - 1) (eq-gpe-num); 0: beta |psi|^2 (Sec. 4.3) */
+} gp_field_params;
+
+typedef struct gp_plan gp_plan;
+
+typedef struct {
+  double N;        /* <|psi|^2>                                   (eq-scaling-N) */
+  double E;        /* <2 alpha^2 |grad psi|^2 + alpha beta (|psi|^2-1)^2> (eq-scaling-energy) */
+  double E_kin;    /* <|sqrt(rho) v|^2 / 2>                       (eq-scaling-energy-mod-rho) */
+  double E_kin_i;  /* incompressible part (Helmholtz split)       (eq:def-ekin-decomp) */
+  double E_kin_c;  /* compressible part */
+  double E_q;      /* <2 alpha^2 |grad sqrt(rho)|^2> */
+  double E_int;    /* <alpha beta (rho - 1)^2> */
+} gp_diag;
+
+/* Create a plan for nfields independent fields (a ragged batch is allowed: each
+ * field has its own N, dt and parameters).  cuda_stream is a cudaStream_t or
+ * NULL for the legacy default stream.  Builds twiddle and propagator tables
+ * (float64 generation, rounded to the storage type).  *out receives the plan.
+ * Errors: GP_ERR_INVALID_ARG, GP_ERR_UNSUPPORTED_SIZE, GP_ERR_OOM, GP_ERR_CUDA. */
+gp_status gp_plan_create(const gp_field_params* fields, int nfields, void* cuda_stream, gp_plan** out);
+
+/* Free every resource of the plan (tables, workspaces, graphs).  NULL is a no-op. */
+gp_status gp_plan_destroy(gp_plan* plan);
+
+/* Number of spectral shells of a field: floor(sqrt(3) N / 2 + 1/2) + 1. */
+int gp_plan_nbins(const gp_plan* plan, int field);
+
+/* Derived alpha and beta actually used by a field (host values). */
+gp_status gp_plan_coefficients(const gp_plan* plan, int field, double* alpha, double* beta);
+
+/* Smoothed-random-phase initial condition psi = exp(i theta) (Sec. 5.3, SRP_Init).
+ *   mode 0 (spectral): theta = Gaussian noise filtered by exp(-|k|^2 / p0^2) in Fourier
+ *          space, zero mean, scaled to RMS p1 (p0 = k0, p1 = theta_rms).
+ *   mode 1 (paper): theta uniform in [-p0, p0] on an N_r^3 lattice (N_r = (int)p1,
+ *          N divisible by N_r), periodic cubic-spline interpolation along x, y, z.
+ * Random numbers: SplitMix64 stream positions seed * 2^40 + i (Steele, Lea & Flood 2014).
+ * Generation runs in float64 and is rounded to the field's storage type.
+ * psi: device field of the plan's precision, written in full. */
+gp_status gp_init_srp(gp_plan* plan, int field, void* psi, uint64_t seed, int mode, double p0, double p1);
+
+/* Random-vortex-ring initial condition (Sec. 5.4).
+ *   mode 0 (rings): `count` rings, radius uniform in [p0, p1], centre uniform in the box,
+ *          normal uniform on the sphere; psi = prod_j tanh(s_j/(sqrt2 xi)) exp(i atan2(z'_j, rho'_j - R_j))
+ *          with the minimum-image displacement to ring j.
+ *   mode 1 (paper): `count` Pade vortex-ring pairs of radius p0 and separation p1 with their
+ *          six mirror images, each shifted by a random vector (Fourier shift) and given one
+ *          of six axis orders, multiplied together.
+ * psi: device field of the plan's precision, written in full. */
+gp_status gp_init_rvr(gp_plan* plan, int field, void* psi, uint64_t seed, int mode, int count, double p0, double p1);
+
+/* psi = exp(i theta) for a real field theta (float for GP_FP32, double for GP_FP64). */
+gp_status gp_psi_from_phase(gp_plan* plan, int field, const void* theta, void* psi);
+
+/* Advance every field of the plan by nsteps time steps, in place.
+ * psi[f] is the device field of field f.  nsteps >= 0.  Asynchronous. */
+gp_status gp_step(gp_plan* plan, void* const* psi, int nsteps);
+
+/* Same as gp_step for host-resident fields: copies each field to a plan-owned
+ * device buffer, steps, copies back, and synchronises.  psi_host[f] points to
+ * n^3 complex values of the field's precision (pinned memory is fastest). */
+gp_status gp_step_host(gp_plan* plan, void* const* psi_host, int nsteps);
+
+/* Diagnostics of one field (Sec. 3.4-3.5 and 4.1), float64 reductions.
+ * out: host record.  spectra: NULL or host array of 4*nbins doubles receiving the
+ * shell spectra E_kin^i, E_kin^c, E_q, E_int (in that order), nbins = gp_plan_nbins.
+ * Readings where the paper is silent: first derivatives use Nyquist-zeroed
+ * wavenumbers; sqrt(rho) v = 2 alpha Im(psi* grad psi)/|psi| and grad sqrt(rho) =
+ * Re(psi* grad psi)/|psi|, zero where |psi|^2 < 1e-12; the k = 0 mode of the
+ * Helmholtz split is incompressible; shell b = floor(|k| + 1/2).
+ * Synchronises the plan's stream.  GP_ERR_NONFINITE if psi holds NaN/Inf. */
+gp_status gp_diagnostics(gp_plan* plan, int field, const void* psi, gp_diag* out, double* spectra, int nbins);
+
+/* Adjoint of nsteps split steps (no counterpart in the paper: the transpose of
+ * the Sec. 4.3 step under <a, b> = Re sum conj(a) b).
+ *   psi_n:  device field, the state at the start of the nsteps steps (read only);
+ *   lambda: device field; on entry the cotangent at the end of the steps, on
+ *           return the cotangent at their start.
+ * The states inside the segment are recomputed from psi_n into a plan-owned
+ * workspace of nsteps fields (the caller checkpoints segments).  Per step:
+ *   VJP_K(s) lam = K(-s) lam;
+ *   VJP_N(s) lam = exp(+i phi) lam + 2 beta s Im(conj(lam) psi_out) psi,  phi = beta s (|psi|^2 - c). */
+gp_status gp_adjoint_step(gp_plan* plan, int field, const void* psi_n, void* lambda, int nsteps);
+
+/* Gradient of J = E_kin^i(psi) with |psi| regularised as sqrt(|psi|^2 + eps) inside
+ * sqrt(rho) v: writes lambda_out = dJ/dpsi (device field) and, if J_out != NULL,
+ * J (host, synchronises).  eps > 0. */
+gp_status gp_ekin_i_grad(gp_plan* plan, int field, const void* psi, void* lambda_out, double eps, double* J_out);
+
+/* dJ/dtheta = -Im(conj(lambda) psi) for psi = exp(i theta): real output field
+ * (float for GP_FP32, double for GP_FP64). */
+gp_status gp_phase_grad(gp_plan* plan, int field, const void* psi, const void* lambda, void* grad_theta);
+
+/* Instrumentation (no counterpart in the paper).
+ * gp_profile(plan, 1) clears the records and makes later gp_step calls launch every
+ * float32 sweep directly (no graph replay) between a pair of CUDA events on the plan's
+ * stream; gp_profile(plan, 0) stops recording.  gp_profile_read synchronises the stream
+ * and reports, per sweep kind (kernel, operation, axis), the number of launches and their
+ * summed device time in milliseconds.  names receives max_kinds NUL-terminated strings of
+ * 64 bytes each.  Returns the number of kinds written, or -1 on error. */
+gp_status gp_profile(gp_plan* plan, int enable);
+int gp_profile_read(gp_plan* plan, int max_kinds, char* names, long long* launches, double* ms);
+
+/* Number of kernels this plan has launched (or replayed inside graphs) since creation. */
+long long gp_launch_count(const gp_plan* plan);
+
+/* Message of the last failed call on this plan ("" if none); valid until the next call. */
+const char* gp_last_error(const gp_plan* plan);
+
+/* Static name of a status code. */
+const char* gp_status_string(gp_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GP_H */

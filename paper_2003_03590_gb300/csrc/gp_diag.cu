@@ -1,0 +1,252 @@
+// gp_diag.cu -- energy, mass and spectra of one field with float64 reductions.
+//
+// Quantities (volume means; Sec. 4.1 eq-scaling-N, eq-scaling-energy, eq-scaling-energy-mod-rho;
+// Sec. 3.4 eq:def-ekin-decomp; Sec. 3.5 spectra).  With n = N^3 points and the unnormalised
+// forward DFT F, Parseval gives <|f|^2> = sum_k |F f|^2 / n^2:
+//   N     = <|psi|^2>
+//   E     = 2 alpha^2 sum_k |k|^2 |F psi|^2 / n^2 + alpha beta <(|psi|^2 - 1)^2>
+//   u     = sqrt(rho) v = 2 alpha Im(psi* grad psi) / |psi|,  q = grad sqrt(rho) = Re(psi* grad psi) / |psi|
+//           (grad with Nyquist-zeroed wavenumbers; u = q = 0 where |psi|^2 < 1e-12)
+//   E_kin = <|u|^2 / 2>,  E_q = <2 alpha^2 |q|^2>,  E_int = <alpha beta (rho - 1)^2>
+//   Helmholtz: u^c_k = k~ (k~ . u_k) / |k~|^2 (k = 0 incompressible), u^i = u - u^c
+//   shell b = floor(|k| + 1/2): E_kin^{i,c}(b) = sum |u^{i,c}_k|^2 / (2 n^2),
+//   E_q(b) = 2 alpha^2 sum_j |F q_j|^2 / n^2,  E_int(b) = alpha beta |F(rho - 1)|^2 / n^2.
+// Pipeline: 8 complex 3D FFTs; the two real fields u_j and q_j share one complex
+// transform (W_j = u_j + i q_j) and are separated with the mirror mode -k.
+#include <cmath>
+#include <vector>
+
+#include "gp_internal.h"
+
+namespace gp {
+
+constexpr double EPS_RHO = 1e-12;
+
+__device__ __forceinline__ int wavenumber(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
+__device__ __forceinline__ int wavenumber_d(int i, int n) { return (2 * i == n) ? 0 : wavenumber(i, n); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-reduce NA partial sums and add them to acc[0..NA)
+template <int NA> __device__ __forceinline__ void block_add(double (&v)[NA], double* acc) {
+  __shared__ double red[NA][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    double s = warp_sum(v[a]);
+    if (lane == 0) red[a][w] = s;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      double s = lane < nw ? red[a][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) atomicAdd(acc + a, s);
+    }
+  }
+}
+
+static inline unsigned rgrid(long long n) {
+  long long b = (n + 255) / 256;
+  return (unsigned)(b < 1 ? 1 : (b > 152LL * 16 ? 152LL * 16 : b));
+}
+
+// sum |psi|^2, sum (|psi|^2 - 1)^2; flags non-finite input
+template <typename T> __global__ void k_phys1(const cpx<T>* __restrict__ psi, long long npts, double* acc, int* flag) {
+  double v[2] = {0.0, 0.0};
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
+    cpx<T> a = psi[i];
+    double r = (double)a.x * a.x + (double)a.y * a.y;
+    bad |= !isfinite(r);
+    v[0] += r;
+    v[1] += (r - 1.0) * (r - 1.0);
+  }
+  if (bad) atomicOr(flag, 1);
+  block_add<2>(v, acc);
+}
+
+// sum |k|^2 |psi_k|^2 (true |k|, Nyquist kept); W_j = i k~_j psi_k
+template <typename T>
+__global__ void k_kspace1(const cpx<T>* __restrict__ ph, cpx<T>* w1, cpx<T>* w2, cpx<T>* w3, int n, double* acc) {
+  const long long npts = (long long)n * n * n;
+  double v[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
+    const double kx = wavenumber(ix, n), ky = wavenumber(iy, n), kz = wavenumber(iz, n);
+    cpx<T> a = ph[i];
+    v[0] += (kx * kx + ky * ky + kz * kz) * ((double)a.x * a.x + (double)a.y * a.y);
+    const T dx = (T)wavenumber_d(ix, n), dy = (T)wavenumber_d(iy, n), dz = (T)wavenumber_d(iz, n);
+    w1[i] = cpx<T>{-dx * a.y, dx * a.x};
+    w2[i] = cpx<T>{-dy * a.y, dy * a.x};
+    w3[i] = cpx<T>{-dz * a.y, dz * a.x};
+  }
+  block_add<1>(v, acc);
+}
+
+// u_j, q_j packed as W_j = u_j + i q_j; W0 = rho - 1; sums of |u|^2 / 2 and 2 alpha^2 |q|^2
+template <typename T>
+__global__ void k_phys2(const cpx<T>* __restrict__ psi, cpx<T>* w0, cpx<T>* w1, cpx<T>* w2, cpx<T>* w3, long long npts,
+                        double alpha, double* acc) {
+  double v[2] = {0.0, 0.0};
+  const T a2 = (T)(2.0 * alpha);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
+    cpx<T> p = psi[i];
+    const T rho = p.x * p.x + p.y * p.y;
+    cpx<T>* ws[3] = {w1, w2, w3};
+    const bool ok = (double)rho >= EPS_RHO;
+    const T inv_amp = ok ? T(1) / sqrt(rho) : T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cpx<T> g = ws[j][i];
+      const T re = p.x * g.x + p.y * g.y;   // Re(conj(psi) g)
+      const T im = p.x * g.y - p.y * g.x;   // Im(conj(psi) g)
+      const T u = a2 * im * inv_amp, q = re * inv_amp;
+      ws[j][i] = cpx<T>{u, q};
+      v[0] += 0.5 * (double)u * u;
+      v[1] += 2.0 * alpha * alpha * (double)q * q;
+    }
+    w0[i] = cpx<T>{rho - T(1), T(0)};
+  }
+  block_add<2>(v, acc);
+}
+
+// Helmholtz split and shell binning; spec layout [4][nbins]: E_kin^i, E_kin^c, E_q, E_int (unscaled)
+template <typename T>
+__global__ void k_kspace2(const cpx<T>* __restrict__ w0, const cpx<T>* __restrict__ w1, const cpx<T>* __restrict__ w2,
+                          const cpx<T>* __restrict__ w3, int n, int nbins, double alpha, double beta, double* spec) {
+  extern __shared__ double hist[];
+  for (int b = threadIdx.x; b < 4 * nbins; b += blockDim.x) hist[b] = 0.0;
+  __syncthreads();
+  const long long npts = (long long)n * n * n;
+  const cpx<T>* ws[3] = {w1, w2, w3};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
+    const int mx = (n - ix) % n, my = (n - iy) % n, mz = (n - iz) % n;
+    const long long im = ((long long)mz * n + my) * n + mx;
+    const double kx = wavenumber(ix, n), ky = wavenumber(iy, n), kz = wavenumber(iz, n);
+    int b = (int)floor(sqrt(kx * kx + ky * ky + kz * kz) + 0.5);
+    if (b >= nbins) b = nbins - 1;
+    const double kd[3] = {(double)wavenumber_d(ix, n), (double)wavenumber_d(iy, n), (double)wavenumber_d(iz, n)};
+    double ur[3], ui[3], eq = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cpx<T> z = ws[j][i], zm = ws[j][im];
+      // u_k = (Z(k) + conj(Z(-k))) / 2,  q_k = (Z(k) - conj(Z(-k))) / (2 i)
+      ur[j] = 0.5 * ((double)z.x + zm.x);
+      ui[j] = 0.5 * ((double)z.y - zm.y);
+      const double qr = 0.5 * ((double)z.y + zm.y), qi = -0.5 * ((double)z.x - zm.x);
+      eq += qr * qr + qi * qi;
+    }
+    const double kk = kd[0] * kd[0] + kd[1] * kd[1] + kd[2] * kd[2];
+    double cr = 0.0, ci = 0.0;
+    if (kk > 0.0) {
+      cr = (kd[0] * ur[0] + kd[1] * ur[1] + kd[2] * ur[2]) / kk;
+      ci = (kd[0] * ui[0] + kd[1] * ui[1] + kd[2] * ui[2]) / kk;
+    }
+    double ei = 0.0, ec = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double ucr = kd[j] * cr, uci = kd[j] * ci;
+      ec += ucr * ucr + uci * uci;
+      const double uir = ur[j] - ucr, uii = ui[j] - uci;
+      ei += uir * uir + uii * uii;
+    }
+    cpx<T> r = w0[i];
+    atomicAdd(&hist[b], 0.5 * ei);
+    atomicAdd(&hist[nbins + b], 0.5 * ec);
+    atomicAdd(&hist[2 * nbins + b], 2.0 * alpha * alpha * eq);
+    atomicAdd(&hist[3 * nbins + b], alpha * beta * ((double)r.x * r.x + (double)r.y * r.y));
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 4 * nbins; b += blockDim.x)
+    if (hist[b] != 0.0) atomicAdd(&spec[b], hist[b]);
+}
+
+template <typename T>
+static gp_status diag_impl(gp_plan* p, int field, const cpx<T>* psi, gp_diag* out, double* spectra, int nbins_req) {
+  FieldPlan& F = p->f[field];
+  const long long npts = F.npts;
+  const int n = F.n;
+  const int nbins = gp_plan_nbins(p, field);
+  cudaStream_t s = p->stream;
+  const size_t fb = (size_t)npts * sizeof(cpx<T>);
+  gp_status st = ensure_ws(p, field, 4 * fb + (size_t)4 * nbins * sizeof(double));
+  if (st != GP_OK) return st;
+  cpx<T>* w0 = (cpx<T>*)F.ws;
+  cpx<T>* w1 = w0 + npts;
+  cpx<T>* w2 = w1 + npts;
+  cpx<T>* w3 = w2 + npts;
+  double* spec = (double*)(w3 + npts);
+  GP_CUDA(p, cudaMemsetAsync(p->acc, 0, 8 * sizeof(double), s));
+  GP_CUDA(p, cudaMemsetAsync(p->flag, 0, sizeof(int), s));
+  GP_CUDA(p, cudaMemsetAsync(spec, 0, (size_t)4 * nbins * sizeof(double), s));
+  k_phys1<T><<<rgrid(npts), 256, 0, s>>>(psi, npts, p->acc, p->flag);
+  GP_CUDA(p, cudaGetLastError());
+  GP_CUDA(p, cudaMemcpyAsync(w0, psi, fb, cudaMemcpyDeviceToDevice, s));
+  GP_CUDA(p, fft3<T>(F, w0, false, s));
+  k_kspace1<T><<<rgrid(npts), 256, 0, s>>>(w0, w1, w2, w3, n, p->acc + 2);
+  GP_CUDA(p, cudaGetLastError());
+  GP_CUDA(p, fft3<T>(F, w1, true, s));
+  GP_CUDA(p, fft3<T>(F, w2, true, s));
+  GP_CUDA(p, fft3<T>(F, w3, true, s));
+  k_phys2<T><<<rgrid(npts), 256, 0, s>>>(psi, w0, w1, w2, w3, npts, F.alpha, p->acc + 3);
+  GP_CUDA(p, cudaGetLastError());
+  GP_CUDA(p, fft3<T>(F, w0, false, s));
+  GP_CUDA(p, fft3<T>(F, w1, false, s));
+  GP_CUDA(p, fft3<T>(F, w2, false, s));
+  GP_CUDA(p, fft3<T>(F, w3, false, s));
+  const size_t hsm = (size_t)4 * nbins * sizeof(double);
+  if (hsm > 48 * 1024) GP_CUDA(p, cudaFuncSetAttribute(k_kspace2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+  k_kspace2<T><<<rgrid(npts), 256, hsm, s>>>(w0, w1, w2, w3, n, nbins, F.alpha, F.beta, spec);
+  GP_CUDA(p, cudaGetLastError());
+  double acc[8];
+  int flag = 0;
+  std::vector<double> hs((size_t)4 * nbins);
+  GP_CUDA(p, cudaMemcpyAsync(acc, p->acc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(p, cudaMemcpyAsync(&flag, p->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(p, cudaMemcpyAsync(hs.data(), spec, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(p, cudaStreamSynchronize(s));
+  if (flag) return fail(p, GP_ERR_NONFINITE, "gp_diagnostics: field holds NaN or Inf");
+  const double dn = (double)npts, dn2 = dn * dn;
+  gp_diag d{};
+  d.N = acc[0] / dn;
+  d.E_int = F.alpha * F.beta * acc[1] / dn;
+  d.E = 2.0 * F.alpha * F.alpha * acc[2] / dn2 + d.E_int;
+  d.E_kin = acc[3] / dn;
+  d.E_q = acc[4] / dn;
+  double si = 0.0, sc = 0.0;
+  for (int b = 0; b < nbins; ++b) {
+    si += hs[b];
+    sc += hs[nbins + b];
+  }
+  d.E_kin_i = si / dn2;
+  d.E_kin_c = sc / dn2;
+  *out = d;
+  if (spectra) {
+    const int nb = nbins_req < nbins ? nbins_req : nbins;
+    for (int q = 0; q < 4; ++q)
+      for (int b = 0; b < nb; ++b) spectra[q * nbins_req + b] = hs[(size_t)q * nbins + b] / dn2;
+  }
+  return GP_OK;
+}
+
+}  // namespace gp
+
+using namespace gp;
+
+extern "C" gp_status gp_diagnostics(gp_plan* p, int field, const void* psi, gp_diag* out, double* spectra, int nbins) {
+  if (!p) return GP_ERR_INVALID_ARG;
+  if (field < 0 || field >= (int)p->f.size()) return fail(p, GP_ERR_INVALID_ARG, "gp_diagnostics: field index");
+  if (!psi || ((uintptr_t)psi & 15) || !out) return fail(p, GP_ERR_INVALID_ARG, "gp_diagnostics: pointer");
+  if (spectra && nbins < gp_plan_nbins(p, field))
+    return fail(p, GP_ERR_INVALID_ARG, "gp_diagnostics: nbins smaller than gp_plan_nbins");
+  if (p->f[field].fp64) return diag_impl<double>(p, field, (const cpx<double>*)psi, out, spectra, nbins);
+  return diag_impl<float>(p, field, (const cpx<float>*)psi, out, spectra, nbins);
+}

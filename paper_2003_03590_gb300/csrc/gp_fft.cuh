@@ -1,0 +1,307 @@
+// gp_fft.cuh -- register-resident Stockham FFT along one axis of a tile of pencils.
+//
+// The pseudo-spectral step of Sec. 4.3 (eq:adi_looptime) needs 1D DFTs along
+// x, y and z of an N^3 complex field, unnormalised forward
+//   X[k] = sum_j x[j] exp(-2 pi i j k / N)
+// and inverse with exp(+...) and a 1/N factor.  A CTA owns B pencils of
+// length L.  Each thread owns E = L / TP elements of one pencil in registers;
+// a radix-R pass turns those into E/R radix-R butterflies, and consecutive
+// passes exchange data through shared memory.  The pass with radix R and
+// "span" NS (product of the radices already applied) follows the autosort
+// (Stockham) indexing: butterfly j reads x[j + r L/R] (r < R), multiplies by
+// w^(r (j mod NS)) with w = exp(-+ 2 pi i / (NS R)), does a radix-R DFT and
+// writes y[(j / NS) NS R + (j mod NS) + r NS].  The first pass reads and the
+// last pass writes natural order, so
+//   * the inverse transform uses the radices in reverse order; its last pass
+//     then leaves in registers exactly the element pattern the first forward
+//     pass reads, and a pointwise operation between them (the nonlinear phase
+//     of Sec. 4.3) costs no data movement;
+//   * the same holds between a forward transform and an inverse one (the
+//     kinetic propagator of Sec. 4.3).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gp {
+
+template <typename T> struct CT;
+template <> struct CT<float> { using v = float2; };
+template <> struct CT<double> { using v = double2; };
+template <typename T> using cpx = typename CT<T>::v;
+
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename V> __device__ __forceinline__ V cmulconj(V a, V b) {  // a * conj(b)
+  return V{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) { return V{a.x * s, a.y * s}; }
+template <typename V> __device__ __forceinline__ V cneg(V a) { return V{-a.x, -a.y}; }
+// a * (-i) for the forward direction, a * (+i) for the inverse one
+template <bool INV, typename V> __device__ __forceinline__ V mul_mi(V a) {
+  return INV ? V{-a.y, a.x} : V{a.y, -a.x};
+}
+// ---------------------------------------------------------------- unbiased constants
+// A float32 constant is carried as hi + lo (hi = nearest float, lo = the rest) and
+// multiplied as fma(x, hi, x * lo): the product is then rounded once, without the
+// fixed relative error of the rounded constant.  A fixed error would bias |w|^2
+// the same way in every step and make the mass (conserved exactly by the
+// scheme) drift linearly in time; the compensated product leaves only unbiased
+// round-off.  float64 uses the constant directly.
+struct KConst {
+  double v;
+  float hi, lo;
+};
+__host__ __device__ constexpr KConst kconst(double v) {
+  return KConst{v, (float)v, (float)(v - (double)(float)v)};
+}
+__device__ __forceinline__ float kmul(float x, KConst k) { return fmaf(x, k.hi, x * k.lo); }
+__device__ __forceinline__ double kmul(double x, KConst k) { return x * k.v; }
+
+// a * (c - i s) forward, a * (c + i s) inverse, for constants c = cos(theta), s = sin(theta)
+template <bool INV, typename V> __device__ __forceinline__ V rotk(V a, KConst c, KConst s) {
+  if constexpr (sizeof(a.x) == 4) {
+    const float re_lo = a.x * c.lo + (INV ? -a.y * s.lo : a.y * s.lo);
+    const float im_lo = a.y * c.lo + (INV ? a.x * s.lo : -a.x * s.lo);
+    const float re = fmaf(a.x, c.hi, fmaf(INV ? -a.y : a.y, s.hi, re_lo));
+    const float im = fmaf(a.y, c.hi, fmaf(INV ? a.x : -a.x, s.hi, im_lo));
+    return V{re, im};
+  } else {
+    return INV ? V{a.x * c.v - a.y * s.v, a.y * c.v + a.x * s.v} : V{a.x * c.v + a.y * s.v, a.y * c.v - a.x * s.v};
+  }
+}
+// multiplication by exp(-+ i pi/4) and exp(-+ 3 i pi/4): one constant, 1/sqrt(2)
+constexpr KConst K_R2 = kconst(0.70710678118654752440);
+constexpr KConst K_C16 = kconst(0.92387953251128675613);   // cos(pi/8)
+constexpr KConst K_S16 = kconst(0.38268343236508977173);   // sin(pi/8)
+constexpr KConst K_H3 = kconst(0.86602540378443864676);    // sqrt(3)/2
+template <bool INV, typename V> __device__ __forceinline__ V rot45(V a) {   // * exp(-+ i pi/4)
+  return INV ? V{kmul(a.x - a.y, K_R2), kmul(a.x + a.y, K_R2)} : V{kmul(a.x + a.y, K_R2), kmul(a.y - a.x, K_R2)};
+}
+template <bool INV, typename V> __device__ __forceinline__ V rot135(V a) {  // * exp(-+ 3 i pi/4)
+  return INV ? V{kmul(-a.x - a.y, K_R2), kmul(a.x - a.y, K_R2)} : V{kmul(a.y - a.x, K_R2), kmul(-a.x - a.y, K_R2)};
+}
+
+// Stockham twiddle storage: float32 keeps hi (x, y) and lo (z, w) parts, float64 the value.
+template <typename T> struct TwT;
+template <> struct TwT<float> { using v = float4; };
+template <> struct TwT<double> { using v = double2; };
+template <typename T> using tw_t = typename TwT<T>::v;
+
+__device__ __forceinline__ float2 twmul(float2 a, float4 w) {   // a * (w.hi + w.lo), one rounding
+  const float re_lo = a.x * w.z - a.y * w.w;
+  const float im_lo = a.x * w.w + a.y * w.z;
+  return float2{fmaf(a.x, w.x, fmaf(-a.y, w.y, re_lo)), fmaf(a.x, w.y, fmaf(a.y, w.x, im_lo))};
+}
+__device__ __forceinline__ double2 twmul(double2 a, double2 w) { return cmul(a, w); }
+
+// ---------------------------------------------------------------- butterflies
+// In-register DFTs of size 2, 3, 4, 8, 16, natural order in and out.
+template <bool INV, typename V> __device__ __forceinline__ void dft2(V& a, V& b) {
+  V t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft4(V& a0, V& a1, V& a2, V& a3) {
+  V s0 = cadd(a0, a2), d0 = csub(a0, a2), s1 = cadd(a1, a3), d1 = mul_mi<INV>(csub(a1, a3));
+  a0 = cadd(s0, s1);
+  a2 = csub(s0, s1);
+  a1 = cadd(d0, d1);
+  a3 = csub(d0, d1);
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft3(V& a0, V& a1, V& a2) {
+  using S = decltype(a0.x);
+  V t1 = cadd(a1, a2);
+  V t2 = V{a0.x - S(0.5) * t1.x, a0.y - S(0.5) * t1.y};
+  V d = csub(a1, a2);
+  V t3 = V{kmul(d.x, K_H3), kmul(d.y, K_H3)};   // (a1 - a2) sqrt(3)/2
+  V it3 = V{-t3.y, t3.x};  // i t3
+  a0 = cadd(a0, t1);
+  if (!INV) { a1 = csub(t2, it3); a2 = cadd(t2, it3); }
+  else      { a1 = cadd(t2, it3); a2 = csub(t2, it3); }
+}
+
+template <bool INV, typename V> __device__ __forceinline__ void dft8(V* v) {
+  V e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  V o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  o1 = rot45<INV>(o1);          // w8^1
+  o2 = mul_mi<INV>(o2);         // w8^2
+  o3 = rot135<INV>(o3);         // w8^3
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+// 16 = 4 x 4: DFT4 over the stride-4 subsequences, twiddles w16^(n2 k1), DFT4 over n2.
+template <bool INV, typename V> __device__ __forceinline__ void dft16(V* v) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+  // now v[4 k1 + n2] = Y[n2][k1]; multiply by w16^(n2 k1)
+  v[5] = rotk<INV>(v[5], K_C16, K_S16);    // n2=1,k1=1: w^1
+  v[6] = rot45<INV>(v[6]);                 // n2=2,k1=1: w^2
+  v[7] = rotk<INV>(v[7], K_S16, K_C16);    // n2=3,k1=1: w^3
+  v[9] = rot45<INV>(v[9]);                 // n2=1,k1=2: w^2
+  v[10] = mul_mi<INV>(v[10]);              // n2=2,k1=2: w^4
+  v[11] = rot135<INV>(v[11]);              // n2=3,k1=2: w^6
+  v[13] = rotk<INV>(v[13], K_S16, K_C16);  // n2=1,k1=3: w^3
+  v[14] = rot135<INV>(v[14]);              // n2=2,k1=3: w^6
+  v[15] = cneg(rotk<INV>(v[15], K_C16, K_S16));  // n2=3,k1=3: w^9 = -w^1
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  // v[4 k1 + k2] = X[k1 + 4 k2]: transpose to natural order
+  V t[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = t[i];
+}
+
+template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V* v) {
+  if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+  else if constexpr (R == 3) dft3<INV>(v[0], v[1], v[2]);
+  else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 16) dft16<INV>(v);
+  else static_assert(R == 2, "unsupported radix");
+}
+
+// ---------------------------------------------------------------- radix plans
+// Forward radix order per length; E = elements per thread (a multiple of every radix).
+template <int L> struct Plan;
+template <> struct Plan<8>    { static constexpr int NP = 1, E = 8,  R0 = 8,  R1 = 1,  R2 = 1; };
+template <> struct Plan<12>   { static constexpr int NP = 2, E = 12, R0 = 4,  R1 = 3,  R2 = 1; };
+template <> struct Plan<16>   { static constexpr int NP = 1, E = 16, R0 = 16, R1 = 1,  R2 = 1; };
+template <> struct Plan<24>   { static constexpr int NP = 2, E = 24, R0 = 8,  R1 = 3,  R2 = 1; };
+template <> struct Plan<32>   { static constexpr int NP = 2, E = 8,  R0 = 8,  R1 = 4,  R2 = 1; };
+template <> struct Plan<48>   { static constexpr int NP = 3, E = 12, R0 = 4,  R1 = 4,  R2 = 3; };
+template <> struct Plan<64>   { static constexpr int NP = 2, E = 8,  R0 = 8,  R1 = 8,  R2 = 1; };
+template <> struct Plan<96>   { static constexpr int NP = 3, E = 24, R0 = 8,  R1 = 4,  R2 = 3; };
+template <> struct Plan<128>  { static constexpr int NP = 2, E = 16, R0 = 16, R1 = 8,  R2 = 1; };
+template <> struct Plan<192>  { static constexpr int NP = 3, E = 24, R0 = 8,  R1 = 8,  R2 = 3; };
+template <> struct Plan<256>  { static constexpr int NP = 2, E = 16, R0 = 16, R1 = 16, R2 = 1; };
+template <> struct Plan<512>  { static constexpr int NP = 3, E = 8,  R0 = 8,  R1 = 8,  R2 = 8; };
+template <> struct Plan<1024> { static constexpr int NP = 3, E = 16, R0 = 16, R1 = 16, R2 = 4; };
+
+template <int L> __host__ __device__ constexpr int radix_fwd(int i) {
+  return i == 0 ? Plan<L>::R0 : (i == 1 ? Plan<L>::R1 : Plan<L>::R2);
+}
+// pass i of the inverse transform uses the forward radices in reverse order
+template <int L, bool INV> __host__ __device__ constexpr int radix_of(int i) {
+  return INV ? radix_fwd<L>(Plan<L>::NP - 1 - i) : radix_fwd<L>(i);
+}
+template <int L, bool INV> __host__ __device__ constexpr int span_of(int i) {
+  int ns = 1;
+  for (int k = 0; k < i; ++k) ns *= radix_of<L, INV>(k);
+  return ns;
+}
+// offset of pass i's twiddles in the direction's table: sum over earlier passes of NS (R - 1)
+template <int L, bool INV> __host__ __device__ constexpr int tw_offset(int i) {
+  int off = 0;
+  for (int k = 0; k < i; ++k) off += span_of<L, INV>(k) * (radix_of<L, INV>(k) - 1);
+  return off;
+}
+template <int L, bool INV> __host__ __device__ constexpr int tw_size() { return tw_offset<L, INV>(Plan<L>::NP); }
+
+// ---------------------------------------------------------------- pencil engine
+// Layout functor Lay: int smem_index(int pencil, int pos).  Registers v[E]:
+// at the input of pass i (radix R) v[b R + r] holds x[t + b TP + r L/R].
+template <typename T, int L, int B, class Lay, bool INV, int I>
+__device__ __forceinline__ void pass_compute(cpx<T>* v, int t, const tw_t<T>* __restrict__ tw) {
+  constexpr int R = radix_of<L, INV>(I);
+  constexpr int NS = span_of<L, INV>(I);
+  constexpr int E = Plan<L>::E;
+  constexpr int TP = L / E;
+  if constexpr (NS > 1) {
+    constexpr int OFF = tw_offset<L, INV>(I);
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+      const int j = t + b * TP;
+      const int jm = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        v[b * R + r] = twmul(v[b * R + r], __ldg(tw + OFF + jm * (R - 1) + (r - 1)));
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < E / R; ++b) dft<R, INV>(v + b * R);
+}
+
+// Write pass I's outputs to shared memory at their Stockham positions.
+template <typename T, int L, class Lay, bool INV, int I>
+__device__ __forceinline__ void pass_store(const cpx<T>* v, int t, int p, cpx<T>* sm, const Lay& lay) {
+  constexpr int R = radix_of<L, INV>(I);
+  constexpr int NS = span_of<L, INV>(I);
+  constexpr int E = Plan<L>::E;
+  constexpr int TP = L / E;
+#pragma unroll
+  for (int b = 0; b < E / R; ++b) {
+    const int j = t + b * TP;
+    const int idxD = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[lay(p, idxD + r * NS)] = v[b * R + r];
+  }
+}
+
+// Read pass I's inputs (natural Stockham input pattern) from shared memory.
+template <typename T, int L, class Lay, bool INV, int I>
+__device__ __forceinline__ void pass_load(cpx<T>* v, int t, int p, const cpx<T>* sm, const Lay& lay) {
+  constexpr int R = radix_of<L, INV>(I);
+  constexpr int E = Plan<L>::E;
+  constexpr int TP = L / E;
+#pragma unroll
+  for (int b = 0; b < E / R; ++b) {
+    const int j = t + b * TP;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b * R + r] = sm[lay(p, j + r * (L / R))];
+  }
+}
+
+// Position (along the pencil) of register e at the input of the first pass of
+// direction INV, equal to the position of register e at the output of the
+// last pass of the opposite direction.
+template <int L, bool INV> __device__ __forceinline__ int in_pos(int e, int t) {
+  constexpr int R = radix_of<L, INV>(0);
+  constexpr int TP = L / Plan<L>::E;
+  return t + (e / R) * TP + (e % R) * (L / R);
+}
+// Position of register e at the output of the last pass of direction INV.
+template <int L, bool INV> __device__ __forceinline__ int out_pos(int e, int t) {
+  constexpr int R = radix_of<L, INV>(Plan<L>::NP - 1);
+  constexpr int TP = L / Plan<L>::E;
+  return t + (e / R) * TP + (e % R) * (L / R);
+}
+
+// Full 1D transform of the registers: input pattern in_pos<INV>, output pattern out_pos<INV>.
+// Uses shared memory for the exchanges between passes (two barriers each).
+template <typename T, int L, int B, class Lay, bool INV>
+__device__ __forceinline__ void fft_regs(cpx<T>* v, int t, int p, cpx<T>* sm, const Lay& lay,
+                                         const tw_t<T>* __restrict__ tw) {
+  constexpr int NP = Plan<L>::NP;
+  pass_compute<T, L, B, Lay, INV, 0>(v, t, tw);
+  if constexpr (NP > 1) {
+    pass_store<T, L, Lay, INV, 0>(v, t, p, sm, lay);
+    __syncthreads();
+    pass_load<T, L, Lay, INV, 1>(v, t, p, sm, lay);
+    __syncthreads();
+    pass_compute<T, L, B, Lay, INV, 1>(v, t, tw);
+  }
+  if constexpr (NP > 2) {
+    pass_store<T, L, Lay, INV, 1>(v, t, p, sm, lay);
+    __syncthreads();
+    pass_load<T, L, Lay, INV, 2>(v, t, p, sm, lay);
+    __syncthreads();
+    pass_compute<T, L, B, Lay, INV, 2>(v, t, tw);
+  }
+}
+
+}  // namespace gp

@@ -1,0 +1,13 @@
+// Instantiations of the pencil sweeps for some grid lengths (compiled in parallel).
+#include "gp_internal.h"
+
+namespace gp {
+cudaError_t sweep_f32_64(const SweepArgs<float>& a, cudaStream_t s) { return SweepLaunch<float, 64>::launch(a, s); }
+cudaError_t sweep_f64_64(const SweepArgs<double>& a, cudaStream_t s) { return SweepLaunch<double, 64>::launch(a, s); }
+cudaError_t sweep_f32_96(const SweepArgs<float>& a, cudaStream_t s) { return SweepLaunch<float, 96>::launch(a, s); }
+cudaError_t sweep_f64_96(const SweepArgs<double>& a, cudaStream_t s) { return SweepLaunch<double, 96>::launch(a, s); }
+cudaError_t sweep_f32_128(const SweepArgs<float>& a, cudaStream_t s) { return SweepLaunch<float, 128>::launch(a, s); }
+cudaError_t sweep_f64_128(const SweepArgs<double>& a, cudaStream_t s) { return SweepLaunch<double, 128>::launch(a, s); }
+cudaError_t sweep_f32_192(const SweepArgs<float>& a, cudaStream_t s) { return SweepLaunch<float, 192>::launch(a, s); }
+cudaError_t sweep_f64_192(const SweepArgs<double>& a, cudaStream_t s) { return SweepLaunch<double, 192>::launch(a, s); }
+}  // namespace gp

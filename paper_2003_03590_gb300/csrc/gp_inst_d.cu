@@ -1,0 +1,7 @@
+// Instantiations of the pencil sweeps for some grid lengths (compiled in parallel).
+#include "gp_internal.h"
+
+namespace gp {
+cudaError_t sweep_f32_512(const SweepArgs<float>& a, cudaStream_t s) { return SweepLaunch<float, 512>::launch(a, s); }
+cudaError_t sweep_f64_512(const SweepArgs<double>& a, cudaStream_t s) { return SweepLaunch<double, 512>::launch(a, s); }
+}  // namespace gp

@@ -1,0 +1,98 @@
+// gp_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <string>
+#include <vector>
+
+#include "gp.h"
+#include "gp_sweep.cuh"
+
+namespace gp {
+
+#define GP_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512) X(1024)
+#define GP_DECL_SWEEP(L)                                                   \
+  cudaError_t sweep_f32_##L(const SweepArgs<float>&, cudaStream_t);        \
+  cudaError_t sweep_f64_##L(const SweepArgs<double>&, cudaStream_t);
+GP_SIZES(GP_DECL_SWEEP)
+#undef GP_DECL_SWEEP
+
+bool supported_n(int n);
+int plan_np(int n);           // number of radix passes for length n
+int plan_radix_fwd(int n, int i);
+cudaError_t sweep(int n, const SweepArgs<float>& a, cudaStream_t s);
+cudaError_t sweep(int n, const SweepArgs<double>& a, cudaStream_t s);
+
+// Device tables of one grid length in one precision.
+struct Tables {
+  void* tw_fwd = nullptr;  // Stockham twiddles, forward direction
+  void* tw_inv = nullptr;  // inverse direction
+};
+
+// Kinetic propagator table exp(-i alpha k^2 s) for a given s, per storage type.
+struct KTable {
+  double s = 0.0;
+  void* dev = nullptr;
+};
+
+struct FieldPlan {
+  gp_field_params prm{};
+  int n = 0;
+  long long npts = 0;
+  double alpha = 0.0, beta = 0.0;
+  bool fp64 = false;
+  Tables t32, t64;                  // both precisions (init and diagnostics use float64)
+  std::vector<KTable> k32, k64;     // cached propagator tables
+  void* host_buf = nullptr;         // device buffer used by gp_step_host
+  void* ws = nullptr;               // general workspace (lazily sized)
+  size_t ws_bytes = 0;
+};
+
+}  // namespace gp
+
+struct gp_plan {
+  std::vector<gp::FieldPlan> f;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double* acc = nullptr;            // device accumulators for reductions
+  int* flag = nullptr;              // device status flags
+  void* adj_ws = nullptr;           // adjoint recompute workspace
+  size_t adj_bytes = 0;
+  cudaGraphExec_t cycle_graph = nullptr;   // captured steady-state cycle of gp_step
+  std::vector<void*> cycle_key;            // field pointers the graph was captured for
+  int cycle_len = 0;
+  long long launches = 0;                  // kernels launched or replayed
+  bool prof = false;                       // per-launch event timing (gp_profile)
+  std::vector<cudaEvent_t> ev_pool;        // recorded events, two per profiled launch
+  std::vector<int> ev_kind;                // kind index of each profiled launch
+  std::vector<std::string> kinds;          // names of the kinds seen
+};
+
+namespace gp {
+
+gp_status fail(gp_plan* p, gp_status st, const std::string& msg);
+gp_status cuda_fail(gp_plan* p, cudaError_t e, const char* what);
+#define GP_CUDA(p, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return gp::cuda_fail(p, e_, #call); \
+  } while (0)
+
+const void* ktable(gp_plan* p, int field, double s, bool fp64);   // device pointer or nullptr
+gp_status ensure_ws(gp_plan* p, int field, size_t bytes);
+
+// 3D transforms of a whole field through the pencil sweeps (unfused).
+template <typename T> cudaError_t fft3(FieldPlan& F, cpx<T>* x, bool inverse, cudaStream_t s);
+// K(s_k) with fused sweeps: fwd z, fwd y, [fwd x, K, 1/N^3, inv x], inv y, inv z.
+template <typename T> cudaError_t kinetic3(FieldPlan& F, cpx<T>* x, double s_k, cudaStream_t s);
+template <typename T> const Tables& tables(FieldPlan& F);
+
+// pointwise kernels (gp_pointwise.cu)
+template <typename T> cudaError_t launch_nonlinear(cpx<T>* psi, long long npts, double coef, double shift, cudaStream_t s);
+template <typename T> cudaError_t launch_kinetic_mul(cpx<T>* psi, int n, const cpx<T>* ek, cudaStream_t s);
+template <typename T> cudaError_t launch_vjp_nonlinear(const cpx<T>* psi_in, cpx<T>* lam, long long npts, double coef,
+                                                       double shift, cudaStream_t s);
+
+// the time step (gp_step.cu): advance one field by nsteps on the plan's stream
+gp_status step_field(gp_plan* p, int field, void* psi, int nsteps);
+
+}  // namespace gp

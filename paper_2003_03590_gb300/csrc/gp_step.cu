@@ -1,0 +1,362 @@
+// gp_step.cu -- the Strang split step (Sec. 4.3, eq:adi_looptime) as a schedule of HBM sweeps.
+//
+// float32 fields (fused): the field stays in a mixed representation between
+// sweeps -- physical along x and y, Fourier along z -- so each step is four
+// sweeps, every one a full read and write of the field:
+//   z: inverse z, N(dt), forward z        y: forward y
+//   x: forward x, K(dt), inverse x        y: inverse y
+// The half-step nonlinear flows of consecutive NKN steps merge into N(dt)
+// (N preserves |psi|, so N(a) N(b) = N(a + b)); the first and last sweeps of a
+// call carry N(dt/2).  The KNK order is the same cycle with K(dt/2) at the two
+// ends: KNK^m = K(h) N(h) [NKN]^(m-1) N(h) K(h).
+// Fields of identical shape and parameters are advanced by the same launches
+// (blockIdx.y selects the field), and the repeating four-sweep cycle is
+// captured once in a CUDA graph and replayed.
+//
+// float64 fields (plain): one kernel per sub-flow and per FFT axis, step by step.
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "gp_internal.h"
+
+namespace gp {
+
+namespace {
+
+struct Group {
+  std::vector<int> fields;
+  int n = 0;
+  bool fp64 = false;
+  int split = 0;
+};
+
+struct Item {
+  int group;
+  int axis;
+  int op;
+  double s_nl;  // time of the nonlinear flow
+  double s_k;   // time of the kinetic flow
+};
+
+bool same_shape(const gp_field_params& a, const gp_field_params& b, const FieldPlan& fa, const FieldPlan& fb) {
+  return a.n == b.n && a.precision == b.precision && a.split == b.split && a.dt == b.dt &&
+         a.nonlin_minus_one == b.nonlin_minus_one && fa.alpha == fb.alpha && fa.beta == fb.beta;
+}
+
+std::vector<Group> make_groups(gp_plan* p) {
+  std::vector<Group> g;
+  for (int i = 0; i < (int)p->f.size(); ++i) {
+    bool placed = false;
+    for (auto& G : g) {
+      const int j = G.fields[0];
+      if ((int)G.fields.size() < GP_MAXB && same_shape(p->f[i].prm, p->f[j].prm, p->f[i], p->f[j])) {
+        G.fields.push_back(i);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) {
+      Group G;
+      G.fields.push_back(i);
+      G.n = p->f[i].n;
+      G.fp64 = p->f[i].fp64;
+      G.split = p->f[i].prm.split;
+      g.push_back(G);
+    }
+  }
+  return g;
+}
+
+gp_status launch_item(gp_plan* p, const Group& G, const Item& it, void* const* psi, cudaStream_t s) {
+  FieldPlan& F = p->f[G.fields[0]];
+  SweepArgs<float> a{};
+  a.count = (int)G.fields.size();
+  for (int k = 0; k < a.count; ++k) a.psi[k] = (cpx<float>*)psi[G.fields[k]];
+  a.tw_fwd = (const tw_t<float>*)F.t32.tw_fwd;
+  a.tw_inv = (const tw_t<float>*)F.t32.tw_inv;
+  a.op = it.op;
+  a.axis = it.axis;
+  a.nl_coef = (float)(F.beta * it.s_nl);
+  a.nl_shift = F.prm.nonlin_minus_one ? 1.0f : 0.0f;
+  a.k_coef = kconst(F.alpha * it.s_k);
+  a.k_norm = kconst(1.0 / (double)F.npts);   // the whole inverse normalisation, applied with K
+  a.scale_inv = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (p->prof) {
+    static const char* opn[] = {"", "fwd", "inv", "inv_n_fwd", "n_fwd", "inv_n", "fwd_k_inv"};
+    std::string name = std::string(it.axis == 0 ? "k_sweep_contig<float," : "k_sweep_strided<float,") +
+                       std::to_string(G.n) + ">:" + opn[it.op] + ":" + "xyz"[it.axis];
+    int kind = -1;
+    for (int q = 0; q < (int)p->kinds.size(); ++q)
+      if (p->kinds[q] == name) kind = q;
+    if (kind < 0) {
+      kind = (int)p->kinds.size();
+      p->kinds.push_back(name);
+    }
+    GP_CUDA(p, cudaEventCreate(&e0));
+    GP_CUDA(p, cudaEventCreate(&e1));
+    GP_CUDA(p, cudaEventRecord(e0, s));
+    p->ev_pool.push_back(e0);
+    p->ev_pool.push_back(e1);
+    p->ev_kind.push_back(kind);
+  }
+  cudaError_t e = sweep(G.n, a, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "sweep launch");
+  if (p->prof) GP_CUDA(p, cudaEventRecord(e1, s));
+  p->launches += 1;
+  return GP_OK;
+}
+
+// the four sweeps that carry K(sk) and then N(sn) to the next cycle
+void k_block(std::vector<Item>& v, int g, double sk) {
+  v.push_back({g, 1, OP_FWD, 0.0, 0.0});
+  v.push_back({g, 0, OP_FWD_K_INV, 0.0, sk});
+  v.push_back({g, 1, OP_INV, 0.0, 0.0});
+}
+
+gp_status run_items(gp_plan* p, const std::vector<Group>& groups, const std::vector<Item>& items, void* const* psi,
+                    cudaStream_t s) {
+  for (const Item& it : items) {
+    gp_status st = launch_item(p, groups[it.group], it, psi, s);
+    if (st != GP_OK) return st;
+  }
+  return GP_OK;
+}
+
+// plain float64 step of one field: N and K as separate kernels, 3D FFTs as three sweeps each
+gp_status plain_steps(gp_plan* p, int field, cpx<double>* psi, int nsteps) {
+  FieldPlan& F = p->f[field];
+  const double dt = F.prm.dt, h = 0.5 * dt;
+  const double shift = F.prm.nonlin_minus_one ? 1.0 : 0.0;
+  const cpx<double>* kd = (const cpx<double>*)ktable(p, field, dt, true);
+  const cpx<double>* kh = (const cpx<double>*)ktable(p, field, h, true);
+  if (!kd || !kh) return fail(p, GP_ERR_OOM, "kinetic table allocation");
+  cudaStream_t s = p->stream;
+  p->launches += (long long)nsteps * (F.prm.split == GP_SPLIT_NKN ? 9 : 15);
+  for (int m = 0; m < nsteps; ++m) {
+    if (F.prm.split == GP_SPLIT_NKN) {
+      GP_CUDA(p, launch_nonlinear<double>(psi, F.npts, F.beta * h, shift, s));
+      GP_CUDA(p, fft3<double>(F, psi, false, s));
+      GP_CUDA(p, launch_kinetic_mul<double>(psi, F.n, kd, s));
+      GP_CUDA(p, fft3<double>(F, psi, true, s));
+      GP_CUDA(p, launch_nonlinear<double>(psi, F.npts, F.beta * h, shift, s));
+    } else {
+      GP_CUDA(p, fft3<double>(F, psi, false, s));
+      GP_CUDA(p, launch_kinetic_mul<double>(psi, F.n, kh, s));
+      GP_CUDA(p, fft3<double>(F, psi, true, s));
+      GP_CUDA(p, launch_nonlinear<double>(psi, F.npts, F.beta * dt, shift, s));
+      GP_CUDA(p, fft3<double>(F, psi, false, s));
+      GP_CUDA(p, launch_kinetic_mul<double>(psi, F.n, kh, s));
+      GP_CUDA(p, fft3<double>(F, psi, true, s));
+    }
+  }
+  return GP_OK;
+}
+
+bool bad_ptr(const void* q) { return q == nullptr || ((uintptr_t)q & 15) != 0; }
+
+}  // namespace
+
+gp_status step_all(gp_plan* p, void* const* psi, int nsteps) {
+  if (nsteps == 0) return GP_OK;
+  std::vector<Group> groups = make_groups(p);
+  cudaStream_t s = p->stream;
+  bool any32 = false;
+  for (int g = 0; g < (int)groups.size(); ++g) {
+    const Group& G = groups[g];
+    if (G.fp64) {
+      for (int f : G.fields) {
+        gp_status st = plain_steps(p, f, (cpx<double>*)psi[f], nsteps);
+        if (st != GP_OK) return st;
+      }
+      continue;
+    }
+    any32 = true;
+  }
+  if (!any32) return GP_OK;
+
+  std::vector<Item> pro, cyc, tail, epi;
+  for (int g = 0; g < (int)groups.size(); ++g) {
+    const Group& G = groups[g];
+    if (G.fp64) continue;
+    const double dt = p->f[G.fields[0]].prm.dt, h = 0.5 * dt;
+    if (G.split == GP_SPLIT_NKN) {
+      pro.push_back({g, 2, OP_N_FWD, h, 0.0});
+      k_block(pro, g, dt);
+      epi.push_back({g, 2, OP_INV_N, h, 0.0});
+    } else {
+      pro.push_back({g, 2, OP_FWD, 0.0, 0.0});
+      k_block(pro, g, h);
+      tail.push_back({g, 2, OP_INV_N_FWD, dt, 0.0});
+      k_block(tail, g, h);
+      epi.push_back({g, 2, OP_INV, 0.0, 0.0});
+    }
+    cyc.push_back({g, 2, OP_INV_N_FWD, dt, 0.0});
+    k_block(cyc, g, dt);
+  }
+  const int ncycles = nsteps - 1;
+
+  gp_status st = run_items(p, groups, pro, psi, s);
+  if (st != GP_OK) return st;
+
+  if (ncycles >= 4 && !p->prof) {
+    // capture the cycle once per set of field pointers, then replay it
+    std::vector<void*> key(psi, psi + p->f.size());
+    if (!p->cycle_graph || p->cycle_key != key) {
+      if (p->cycle_graph) {
+        cudaGraphExecDestroy(p->cycle_graph);
+        p->cycle_graph = nullptr;
+      }
+      cudaStream_t cap;
+      GP_CUDA(p, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const long long before = p->launches;
+        st = run_items(p, groups, cyc, psi, cap);
+        p->launches = before;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (st == GP_OK && e2 != cudaSuccess) st = cuda_fail(p, e2, "cudaStreamEndCapture");
+      } else {
+        st = cuda_fail(p, e, "cudaStreamBeginCapture");
+      }
+      cudaStreamDestroy(cap);
+      if (st != GP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      e = cudaGraphInstantiate(&p->cycle_graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        p->cycle_graph = nullptr;
+        return cuda_fail(p, e, "cudaGraphInstantiate");
+      }
+      p->cycle_key = key;
+    }
+    for (int c = 0; c < ncycles; ++c) GP_CUDA(p, cudaGraphLaunch(p->cycle_graph, s));
+    p->launches += (long long)ncycles * (long long)cyc.size();
+  } else {
+    for (int c = 0; c < ncycles; ++c) {
+      st = run_items(p, groups, cyc, psi, s);
+      if (st != GP_OK) return st;
+    }
+  }
+  st = run_items(p, groups, tail, psi, s);
+  if (st != GP_OK) return st;
+  return run_items(p, groups, epi, psi, s);
+}
+
+gp_status step_field(gp_plan* p, int field, void* psi, int nsteps) {
+  // a one-field view of the plan (used by the adjoint's recomputation)
+  std::vector<void*> ptrs(p->f.size(), nullptr);
+  ptrs[field] = psi;
+  FieldPlan& F = p->f[field];
+  if (F.fp64) return plain_steps(p, field, (cpx<double>*)psi, nsteps);
+  if (nsteps == 0) return GP_OK;
+  Group G;
+  G.fields.push_back(field);
+  G.n = F.n;
+  G.split = F.prm.split;
+  std::vector<Group> groups{G};
+  const double dt = F.prm.dt, h = 0.5 * dt;
+  std::vector<Item> items;
+  if (G.split == GP_SPLIT_NKN) {
+    items.push_back({0, 2, OP_N_FWD, h, 0.0});
+    k_block(items, 0, dt);
+    for (int c = 0; c < nsteps - 1; ++c) {
+      items.push_back({0, 2, OP_INV_N_FWD, dt, 0.0});
+      k_block(items, 0, dt);
+    }
+    items.push_back({0, 2, OP_INV_N, h, 0.0});
+  } else {
+    items.push_back({0, 2, OP_FWD, 0.0, 0.0});
+    k_block(items, 0, h);
+    for (int c = 0; c < nsteps; ++c) {
+      items.push_back({0, 2, OP_INV_N_FWD, dt, 0.0});
+      k_block(items, 0, c == nsteps - 1 ? h : dt);
+    }
+    items.push_back({0, 2, OP_INV, 0.0, 0.0});
+  }
+  return run_items(p, groups, items, ptrs.data(), p->stream);
+}
+
+}  // namespace gp
+
+using namespace gp;
+
+extern "C" {
+
+gp_status gp_step(gp_plan* p, void* const* psi, int nsteps) {
+  if (!p) return GP_ERR_INVALID_ARG;
+  if (!psi || nsteps < 0) return fail(p, GP_ERR_INVALID_ARG, "gp_step: null field list or negative nsteps");
+  for (size_t i = 0; i < p->f.size(); ++i)
+    if (bad_ptr(psi[i])) return fail(p, GP_ERR_INVALID_ARG, "gp_step: field pointer null or not 16-byte aligned");
+  return step_all(p, psi, nsteps);
+}
+
+gp_status gp_step_host(gp_plan* p, void* const* psi_host, int nsteps) {
+  if (!p) return GP_ERR_INVALID_ARG;
+  if (!psi_host || nsteps < 0) return fail(p, GP_ERR_INVALID_ARG, "gp_step_host: null field list or negative nsteps");
+  std::vector<void*> dev(p->f.size());
+  for (size_t i = 0; i < p->f.size(); ++i) {
+    FieldPlan& F = p->f[i];
+    if (!psi_host[i]) return fail(p, GP_ERR_INVALID_ARG, "gp_step_host: null host field");
+    const size_t bytes = (size_t)F.npts * (F.fp64 ? 16 : 8);
+    if (!F.host_buf) GP_CUDA(p, cudaMalloc(&F.host_buf, bytes));
+    dev[i] = F.host_buf;
+    GP_CUDA(p, cudaMemcpyAsync(F.host_buf, psi_host[i], bytes, cudaMemcpyHostToDevice, p->stream));
+  }
+  gp_status st = step_all(p, dev.data(), nsteps);
+  if (st != GP_OK) return st;
+  for (size_t i = 0; i < p->f.size(); ++i) {
+    FieldPlan& F = p->f[i];
+    const size_t bytes = (size_t)F.npts * (F.fp64 ? 16 : 8);
+    GP_CUDA(p, cudaMemcpyAsync(psi_host[i], F.host_buf, bytes, cudaMemcpyDeviceToHost, p->stream));
+  }
+  GP_CUDA(p, cudaStreamSynchronize(p->stream));
+  return GP_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+gp_status gp_profile(gp_plan* p, int enable) {
+  if (!p) return GP_ERR_INVALID_ARG;
+  if (enable) {
+    GP_CUDA(p, p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    p->ev_pool.clear();
+    p->ev_kind.clear();
+    p->kinds.clear();
+  }
+  p->prof = enable != 0;
+  return GP_OK;
+}
+
+int gp_profile_read(gp_plan* p, int max_kinds, char* names, long long* launches, double* ms) {
+  if (!p || max_kinds < 0 || (max_kinds > 0 && (!names || !launches || !ms))) return -1;
+  if ((p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize()) != cudaSuccess) return -1;
+  const int nk = (int)p->kinds.size();
+  std::vector<double> tot(nk, 0.0);
+  std::vector<long long> cnt(nk, 0);
+  for (size_t i = 0; i < p->ev_kind.size(); ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p->ev_pool[2 * i], p->ev_pool[2 * i + 1]) != cudaSuccess) return -1;
+    tot[p->ev_kind[i]] += t;
+    cnt[p->ev_kind[i]] += 1;
+  }
+  const int nout = nk < max_kinds ? nk : max_kinds;
+  for (int q = 0; q < nout; ++q) {
+    std::snprintf(names + 64 * q, 64, "%s", p->kinds[q].c_str());
+    launches[q] = cnt[q];
+    ms[q] = tot[q];
+  }
+  return nout;
+}
+
+long long gp_launch_count(const gp_plan* p) { return p ? p->launches : -1; }
+
+}  // extern "C"

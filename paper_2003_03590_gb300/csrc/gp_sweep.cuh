@@ -1,0 +1,232 @@
+// gp_sweep.cuh -- one HBM sweep over an N^3 field: 1D transforms along one axis with the
+// pointwise sub-flows of the split step (Sec. 4.3) fused into the same pass.
+//
+// Ops (applied to every pencil of the chosen axis, in place):
+//   OP_FWD        forward DFT
+//   OP_INV        inverse DFT (with 1/N)
+//   OP_INV_N_FWD  inverse DFT, nonlinear flow N(s), forward DFT
+//   OP_N_FWD      N(s), forward DFT
+//   OP_INV_N      inverse DFT, N(s)
+//   OP_FWD_K_INV  forward DFT, kinetic flow K(s) (needs every other axis already in
+//                 Fourier space), inverse DFT
+// N(s):  psi <- exp(-i (beta s) (|psi|^2 - c)) psi                 (exact nonlinear flow)
+// K(s):  psi_k <- exp(-i alpha s (kx^2 + ky^2 + kz^2)) psi_k          (exact kinetic flows)
+// The kinetic phase is formed per element from the integer |k|^2 and evaluated
+// with sincos, so its rounding is unbiased; the 1/N^3 of the inverse transform
+// is folded into the same multiplication (the inverse sweeps that follow it in a
+// step then do not scale).
+#pragma once
+#include "gp_fft.cuh"
+
+namespace gp {
+
+enum SweepOp : int { OP_FWD = 1, OP_INV = 2, OP_INV_N_FWD = 3, OP_N_FWD = 4, OP_INV_N = 5, OP_FWD_K_INV = 6 };
+
+constexpr int GP_MAXB = 32;  // fields of one shape handled by one launch (blockIdx.y)
+
+template <typename T> struct SweepArgs {
+  cpx<T>* psi[GP_MAXB];     // device fields, N^3 each, [z][y][x]; field blockIdx.y
+  int count;                // number of fields in psi[]
+  const tw_t<T>* tw_fwd;    // forward Stockham twiddles for length N
+  const tw_t<T>* tw_inv;    // inverse Stockham twiddles for length N
+  KConst k_coef;            // alpha * s of K(s) (OP_FWD_K_INV)
+  KConst k_norm;            // factor applied with K: 1/N^3 (fused step) or 1
+  T nl_coef;                // beta * s of N(s)
+  T nl_shift;               // c of N(s): 1 (eq-gpe-num) or 0
+  int op;
+  int axis;                 // 0: x (contiguous rows), 1: y, 2: z (strided pencils)
+  int scale_inv;            // 1: inverse ops multiply by 1/N; 0: normalisation done with K
+};
+
+template <int L> __device__ __forceinline__ int ksq(int i) {   // squared integer wavenumber of index i
+  const int k = i < (L + 1) / 2 ? i : i - L;
+  return k * k;
+}
+
+// exp(-i coef k2) x, the phase formed from the exact integer k2
+template <typename V> __device__ __forceinline__ V kinetic_phase(V x, KConst coef, KConst norm, int k2) {
+  if constexpr (sizeof(x.x) == 4) {
+    const float kf = (float)k2;
+    const float ph = fmaf(coef.hi, kf, coef.lo * kf);
+    float sn, cs;
+    sincosf(ph, &sn, &cs);
+    V y{x.x * cs + x.y * sn, x.y * cs - x.x * sn};
+    return V{kmul(y.x, norm), kmul(y.y, norm)};
+  } else {
+    double sn, cs;
+    sincos(coef.v * (double)k2, &sn, &cs);
+    V y{x.x * cs + x.y * sn, x.y * cs - x.x * sn};
+    return V{y.x * norm.v, y.y * norm.v};
+  }
+}
+
+template <typename V> __device__ __forceinline__ V kscale(V x, KConst k) { return V{kmul(x.x, k), kmul(x.y, k)}; }
+
+// pencils per CTA
+template <typename T, int L> __host__ __device__ constexpr int strided_batch() {
+  return (L % 16 == 0) ? ((sizeof(T) == 8 && L >= 1024) ? 8 : 16) : (L % 8 == 0 ? 8 : 4);
+}
+template <typename T, int L> __host__ __device__ constexpr int contig_batch() {
+  int b = 256 / (L / Plan<L>::E);
+  b = b > 64 ? 64 : (b < 1 ? 1 : b);
+  while ((L * L) % b) b /= 2;
+  return b;
+}
+template <int L> __host__ __device__ constexpr int contig_pitch() { return L + (L >= 16 ? L / 16 : 1); }
+
+struct LayStrided {  // [pos][pencil]
+  int B;
+  __device__ __forceinline__ int operator()(int p, int pos) const { return pos * B + p; }
+};
+template <int L> struct LayContig {  // [pencil][pos] with one pad element every 16
+  __device__ __forceinline__ int operator()(int p, int pos) const {
+    return p * contig_pitch<L>() + pos + (L >= 16 ? (pos >> 4) : 0);
+  }
+};
+
+template <typename V, typename S> __device__ __forceinline__ V nonlinear(V a, S coef, S shift) {
+  S r2 = a.x * a.x + a.y * a.y;
+  S ph = coef * (r2 - shift);
+  S sn, cs;
+  if constexpr (sizeof(S) == 4) sincosf(ph, &sn, &cs);
+  else sincos(ph, &sn, &cs);
+  return V{a.x * cs + a.y * sn, a.y * cs - a.x * sn};  // a * exp(-i ph)
+}
+
+template <typename T, int L, bool INV, class GetAddr>
+__device__ __forceinline__ void load_pattern(cpx<T>* v, int t, const GetAddr& addr) {
+  constexpr int E = Plan<L>::E;
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = *addr(in_pos<L, INV>(e, t));
+}
+template <typename T, int L, bool INV, class GetAddr>
+__device__ __forceinline__ void store_pattern(const cpx<T>* v, int t, const GetAddr& addr) {
+  constexpr int E = Plan<L>::E;
+#pragma unroll
+  for (int e = 0; e < E; ++e) *addr(out_pos<L, INV>(e, t)) = v[e];
+}
+
+// Body shared by both tile shapes.  k2o is the sum of the squared wavenumbers of the
+// pencil's two other coordinates (only used by OP_FWD_K_INV).
+template <typename T, int L, int B, class Lay, class GetAddr>
+__device__ __forceinline__ void sweep_body(const SweepArgs<T>& a, int t, int p, cpx<T>* sm, const Lay& lay,
+                                           const GetAddr& addr, int k2o) {
+  using V = cpx<T>;
+  constexpr int E = Plan<L>::E;
+  constexpr KConst inv_l = kconst(1.0 / L);
+  const bool sc = a.scale_inv != 0;
+  V v[E];
+  switch (a.op) {
+    case OP_FWD:
+      load_pattern<T, L, false>(v, t, addr);
+      fft_regs<T, L, B, Lay, false>(v, t, p, sm, lay, a.tw_fwd);
+      store_pattern<T, L, false>(v, t, addr);
+      break;
+    case OP_INV:
+      load_pattern<T, L, true>(v, t, addr);
+      fft_regs<T, L, B, Lay, true>(v, t, p, sm, lay, a.tw_inv);
+      if (sc) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = kscale(v[e], inv_l);
+      }
+      store_pattern<T, L, true>(v, t, addr);
+      break;
+    case OP_N_FWD:
+      load_pattern<T, L, false>(v, t, addr);
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = nonlinear(v[e], a.nl_coef, a.nl_shift);
+      fft_regs<T, L, B, Lay, false>(v, t, p, sm, lay, a.tw_fwd);
+      store_pattern<T, L, false>(v, t, addr);
+      break;
+    case OP_INV_N:
+      load_pattern<T, L, true>(v, t, addr);
+      fft_regs<T, L, B, Lay, true>(v, t, p, sm, lay, a.tw_inv);
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = nonlinear(sc ? kscale(v[e], inv_l) : v[e], a.nl_coef, a.nl_shift);
+      store_pattern<T, L, true>(v, t, addr);
+      break;
+    case OP_INV_N_FWD:
+      load_pattern<T, L, true>(v, t, addr);
+      fft_regs<T, L, B, Lay, true>(v, t, p, sm, lay, a.tw_inv);
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = nonlinear(sc ? kscale(v[e], inv_l) : v[e], a.nl_coef, a.nl_shift);
+      __syncthreads();  // shared memory is reused by the forward passes
+      fft_regs<T, L, B, Lay, false>(v, t, p, sm, lay, a.tw_fwd);
+      store_pattern<T, L, false>(v, t, addr);
+      break;
+    case OP_FWD_K_INV:
+      load_pattern<T, L, false>(v, t, addr);
+      fft_regs<T, L, B, Lay, false>(v, t, p, sm, lay, a.tw_fwd);
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = kinetic_phase(v[e], a.k_coef, a.k_norm, k2o + ksq<L>(out_pos<L, false>(e, t)));
+      __syncthreads();
+      fft_regs<T, L, B, Lay, true>(v, t, p, sm, lay, a.tw_inv);
+      store_pattern<T, L, true>(v, t, addr);
+      break;
+    default:
+      break;
+  }
+}
+
+// y or z pencils: a CTA owns B consecutive x of one (z) or (y) line.
+template <typename T, int L>
+__global__ void __launch_bounds__(strided_batch<T, L>() * (L / Plan<L>::E))
+    k_sweep_strided(SweepArgs<T> a) {
+  using V = cpx<T>;
+  constexpr int B = strided_batch<T, L>();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int p = threadIdx.x % B, t = threadIdx.x / B;
+  const int x0 = (blockIdx.x % (L / B)) * B;
+  const int c = blockIdx.x / (L / B);
+  const long st = (a.axis == 1) ? (long)L : (long)L * L;    // stride along the pencil
+  const long sc = (a.axis == 1) ? (long)L * L : (long)L;    // stride of the other coordinate
+  V* base = a.psi[blockIdx.y] + x0 + p + (long)c * sc;
+  auto addr = [&](int pos) { return base + (long)pos * st; };
+  LayStrided lay{B};
+  sweep_body<T, L, B>(a, t, p, sm, lay, addr, ksq<L>(x0 + p) + ksq<L>(c));
+}
+
+// x rows: a CTA owns B consecutive rows (y, z).
+template <typename T, int L>
+__global__ void __launch_bounds__(contig_batch<T, L>() * (L / Plan<L>::E)) k_sweep_contig(SweepArgs<T> a) {
+  using V = cpx<T>;
+  constexpr int TP = L / Plan<L>::E;
+  constexpr int B = contig_batch<T, L>();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int p = threadIdx.x / TP, t = threadIdx.x % TP;
+  const long row = (long)blockIdx.x * B + p;
+  V* base = a.psi[blockIdx.y] + row * L;
+  auto addr = [&](int pos) { return base + pos; };
+  LayContig<L> lay;
+  sweep_body<T, L, B>(a, t, p, sm, lay, addr, ksq<L>((int)(row % L)) + ksq<L>((int)(row / L)));
+}
+
+template <typename T, int L> struct SweepLaunch {
+  static constexpr int TP = L / Plan<L>::E;
+  static constexpr int BS = strided_batch<T, L>();
+  static constexpr int BC = contig_batch<T, L>();
+  static size_t smem_strided() { return sizeof(cpx<T>) * (size_t)L * BS; }
+  static size_t smem_contig() { return sizeof(cpx<T>) * (size_t)contig_pitch<L>() * BC; }
+  static cudaError_t launch(const SweepArgs<T>& a, cudaStream_t s) {
+    if (a.axis == 0) {
+      size_t sm = smem_contig();
+      static bool attr = false;   // set once, outside any stream capture that follows
+      if (!attr && sm > 48 * 1024) cudaFuncSetAttribute(k_sweep_contig<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+      long rows = (long)L * L;
+      k_sweep_contig<T, L><<<dim3((unsigned)(rows / BC), (unsigned)a.count), BC * TP, sm, s>>>(a);
+    } else {
+      size_t sm = smem_strided();
+      static bool attr = false;
+      if (!attr && sm > 48 * 1024) cudaFuncSetAttribute(k_sweep_strided<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+      long tiles = (long)(L / BS) * L;
+      k_sweep_strided<T, L><<<dim3((unsigned)tiles, (unsigned)a.count), BS * TP, sm, s>>>(a);
+    }
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace gp

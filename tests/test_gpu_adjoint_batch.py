@@ -1,0 +1,137 @@
+"""GPU adjoint and gradient against the oracle and finite differences; batched and host-buffer paths."""
+import math
+
+import numpy as np
+import pytest
+
+from inputs import random_direction, random_psi
+from oracle import adjoint as OA
+from oracle import initial as OI
+from oracle import scheme as OS
+from tests._util import rel_l2, to_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2003_03590_gb300 import (GP_FP32, GP_FP64, GP_SPLIT_KNK, GP_SPLIT_NKN, GPEvolve,  # noqa: E402
+                                    IncompressibleKineticEnergy, Plan, field_params)
+
+
+def _op(plan, dt):
+    a, b = plan.coefficients()
+    return OS.Params(n=plan.n(), alpha=a, beta=b, dt=dt)
+
+
+@pytest.mark.parametrize("prec", [GP_FP64, GP_FP32])
+@pytest.mark.parametrize("split", [GP_SPLIT_NKN, GP_SPLIT_KNK])
+def test_adjoint_segment_matches_oracle(prec, split):
+    n, dt, m = 16, 0.004, 5
+    plan = Plan(field_params(n, dt, xi_over_dx=1.5, precision=prec, split=split))
+    dtype = np.complex128 if prec == GP_FP64 else np.complex64
+    psi0 = random_psi(n, 1, amp_jitter=0.2).astype(dtype)
+    lam_T = random_direction(n, 2).astype(dtype)
+    lam = to_gpu(lam_T, dtype)
+    plan.adjoint_step(0, to_gpu(psi0, dtype), lam, m)
+    p = _op(plan, dt)
+    order = "nkn" if split == GP_SPLIT_NKN else "knk"
+    states = OA.forward_states(psi0.astype(np.complex128), p, m, order)
+    ref = lam_T.astype(np.complex128)
+    for k in range(m - 1, -1, -1):
+        ref = OA.vjp_step(states[k], ref, p, order)
+    assert rel_l2(to_np(lam), ref) < (1e-11 if prec == GP_FP64 else 2e-5)
+
+
+@pytest.mark.parametrize("prec", [GP_FP64, GP_FP32])
+def test_ekin_i_gradient_matches_oracle(prec):
+    n = 24
+    plan = Plan(field_params(n, 0.004, xi_over_dx=1.5, precision=prec))
+    dtype = np.complex128 if prec == GP_FP64 else np.complex64
+    psi = random_psi(n, 4, amp_jitter=0.2).astype(dtype)
+    lam, J = plan.ekin_i_grad(0, to_gpu(psi, dtype), 1e-6)
+    p = _op(plan, 0.004)
+    Jr = OA.ekin_i_reg(psi.astype(np.complex128), p)
+    lr = OA.ekin_i_reg_grad(psi.astype(np.complex128), p)
+    tol = 1e-11 if prec == GP_FP64 else 5e-5
+    assert abs(J - Jr) < tol * Jr
+    assert rel_l2(to_np(lam), lr) < tol
+
+
+def test_autograd_gradient_vs_finite_differences_fp64():
+    """dJ/dtheta through the checkpointed adjoint, FP64, vs centred differences (h = 1e-4)."""
+    n, dt, m = 16, 0.004, 12
+    plan = Plan(field_params(n, dt, xi_over_dx=1.5, precision=GP_FP64))
+    theta0 = torch.from_numpy(OI.srp_theta(n, 0, 3.0)).cuda()
+    theta = theta0.clone().requires_grad_(True)
+    psiT = GPEvolve.apply(theta, plan, m, 4)
+    J = IncompressibleKineticEnergy.apply(psiT, plan, 1e-6)
+    J.backward()
+    g = theta.grad.detach()
+
+    def Jof(th):
+        psi = plan.psi_from_phase(0, th)
+        plan.step([psi], m)
+        return plan.ekin_i_grad(0, psi, 1e-6)[1]
+
+    # h = 1e-4 (the configuration's check, relative error <= 1e-3) and h = 1e-5 (tighter: the
+    # state holds near-zeros of psi, where the O(h^2) error of h = 1e-4 is ~1e-4)
+    for seed in range(3):
+        v = torch.from_numpy(np.real(random_direction(n, 50 + seed, complex_valued=False))).cuda()
+        an = float((g * v).sum())
+        for h, tol in ((1e-4, 1e-3), (1e-5, 1e-5)):
+            fd = (Jof(theta0 + h * v) - Jof(theta0 - h * v)) / (2 * h)
+            assert abs(fd - an) < tol * abs(fd), (seed, h, fd, an)
+    # and against the oracle's adjoint gradient
+    Jr, gr = OA.gradient_theta(theta0.cpu().numpy(), _op(plan, dt), m)
+    assert abs(float(J) - Jr) < 1e-10 * Jr
+    assert rel_l2(g.cpu().numpy(), gr) < 1e-8
+
+
+def test_autograd_fp32_vs_fp64_adjoint():
+    n, dt, m = 32, 0.004, 20
+    th = torch.from_numpy(OI.srp_theta(n, 1, 4.0))
+    grads = []
+    for prec, rdt in ((GP_FP64, torch.float64), (GP_FP32, torch.float32)):
+        plan = Plan(field_params(n, dt, xi_over_dx=1.5, precision=prec))
+        t = th.to(rdt).cuda().requires_grad_(True)
+        J = IncompressibleKineticEnergy.apply(GPEvolve.apply(t, plan, m, 5), plan, 1e-6)
+        J.backward()
+        grads.append(t.grad.double().cpu().numpy())
+    assert rel_l2(grads[1], grads[0]) < 1e-3
+
+
+def test_batched_ragged_plan_matches_single_plans_bitwise():
+    dt = 0.004
+    sizes = [16] * 3 + [24] * 2 + [32] * 2
+    fields = [field_params(n, dt, xi_over_dx=1.5) for n in sizes]
+    batch = Plan(fields)
+    psis = [to_gpu(random_psi(n, 10 + i), np.complex64) for i, n in enumerate(sizes)]
+    singles = [p.clone() for p in psis]
+    batch.step(psis, 9)
+    for i, n in enumerate(sizes):
+        Plan(field_params(n, dt, xi_over_dx=1.5)).step([singles[i]], 9)
+        assert torch.equal(psis[i], singles[i]), i
+
+
+def test_host_buffer_step_matches_device_step():
+    n = 32
+    plan = Plan(field_params(n, 0.004, xi_over_dx=1.5))
+    psi0 = random_psi(n, 8).astype(np.complex64)
+    host = torch.from_numpy(psi0.copy()).pin_memory()
+    plan.step_host([host], 6)
+    dev = to_gpu(psi0, np.complex64)
+    plan.step([dev], 6)
+    assert torch.equal(host, dev.cpu())
+
+
+def test_mixed_precision_batch():
+    fields = [field_params(16, 0.004, xi_over_dx=1.5, precision=GP_FP64),
+              field_params(16, 0.004, xi_over_dx=1.5, precision=GP_FP32)]
+    plan = Plan(fields)
+    psi0 = random_psi(16, 3)
+    a = to_gpu(psi0, np.complex128)
+    b = to_gpu(psi0, np.complex64)
+    plan.step([a, b], 5)
+    assert rel_l2(to_np(b), to_np(a)) < 5e-6
