@@ -214,6 +214,77 @@ def roofline_of(gq, plan, psi, n, ksteps, peak):
             "kinds_mean_us": {k: round(ms_ / c_ * 1e3, 2) for k, (c_, ms_) in rec.items()}}
 
 
+def ensemble_leg(gq, steps=500):
+    """24 x 64^3 + 16 x 96^3 + 8 x 128^3 smoothed-random-phase fields (seeds 0..47, k0 = 4),
+    dt = 0.004, advanced together by one plan (one launch per sweep and size class, the
+    four-sweep cycle replayed from a CUDA graph) against the same fields advanced one plan
+    at a time."""
+    import torch
+    sizes = [64] * 24 + [96] * 16 + [128] * 8
+    fields = [gq.field_params(n, 0.004, xi_over_dx=1.5) for n in sizes]
+    batch = gq.Plan(fields)
+    psis = [batch.init_srp(i, batch.empty(i), seed=i, mode=0, p0=4.0, p1=math.pi) for i in range(len(sizes))]
+    pts = sum(n ** 3 for n in sizes)
+    batch.step(psis, 5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = gq.launch_count(batch)
+    e0.record(batch.stream)
+    batch.step(psis, steps)
+    e1.record(batch.stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    launches = gq.launch_count(batch) - l0
+    singles = [gq.Plan(f) for f in fields]
+    for pl, f in zip(singles, psis):
+        pl.step([f], 5)
+    torch.cuda.synchronize()
+    e0.record(singles[0].stream)
+    for pl, f in zip(singles, psis):
+        pl.step([f], steps)
+    e1.record(singles[0].stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    return {"points": pts, "steps": steps, "batched": {"value": pts * steps / (ms_b / 1e3), "ms": ms_b,
+                                                       "launches": launches},
+            "sequential": {"value": pts * steps / (ms_s / 1e3), "ms": ms_s}, "speedup": ms_s / ms_b}
+
+
+def adjoint_leg(gq, n=128, steps=400, every=20):
+    """Gradient of E_kin^i(psi_T) with respect to the initial phase (128^3, 400 steps, checkpoints
+    every 20) through the autograd function, float32 and float64, and their agreement."""
+    import torch
+
+    from inputs import smooth_phase
+    th = torch.from_numpy(smooth_phase(n, 0))
+    out = {}
+    grads = {}
+    for name, prec, rdt in (("fp32", gq.GP_FP32, torch.float32), ("fp64", gq.GP_FP64, torch.float64)):
+        plan = gq.Plan(gq.field_params(n, 0.004, xi_over_dx=1.5, precision=prec))
+        t = th.to(rdt).cuda().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J = gq.IncompressibleKineticEnergy.apply(gq.GPEvolve.apply(t, plan, steps, every), plan, 1e-6)
+        J.backward()
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "J": float(J)}
+        grads[name] = t.grad.double()
+    g32, g64 = grads["fp32"], grads["fp64"]
+    out["grad_rel_err_fp32_vs_fp64"] = float(torch.linalg.vector_norm(g32 - g64) / torch.linalg.vector_norm(g64))
+    return out
+
+
+def diag_leg(gq, plan, psi, n, ms_step, calls=3):
+    import torch
+    plan.diagnostics(0, psi)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        plan.diagnostics(0, psi)
+    ms = (time.perf_counter() - t0) * 1e3 / calls
+    return {"ms_per_call": ms, "share_at_1_per_100_steps": ms / (ms + 100 * ms_step)}
+
+
 def cpu_oracle_baseline(n, dt, steps):
     """The float64 oracle, as it stands, on the host: `steps` full steps of the n^3 workload."""
     from inputs import random_psi
@@ -367,6 +438,9 @@ def main():
             del f, ps
             torch.cuda.empty_cache()
         extras["sizes"] = sizes
+        extras["ensemble"] = ensemble_leg(gq)
+        extras["adjoint_128"] = adjoint_leg(gq)
+        extras["diagnostics_cost"] = diag_leg(gq, plan, psi, n, ms_step)
         # the float64 oracle on the host cores: one full step of the same 256^3 workload
         val, secs = cpu_oracle_baseline(n, DT_MAIN, 1)
         line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -46,3 +46,15 @@ def grid_coords(n):
     x = 2.0 * math.pi * np.arange(n) / n
     Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
     return X, Y, Z
+
+
+def smooth_phase(n, seed, nmodes=24, kmax=4, rms=math.pi):
+    """A real periodic phase field: a few random low Fourier modes scaled to the given RMS."""
+    rng = np.random.default_rng(seed)
+    x = 2.0 * math.pi * np.arange(n) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    th = np.zeros((n, n, n))
+    for _ in range(nmodes):
+        k = rng.integers(-kmax, kmax + 1, size=3)
+        th += rng.standard_normal() * np.cos(k[0] * X + k[1] * Y + k[2] * Z + 2.0 * math.pi * rng.random())
+    return th * (rms / math.sqrt(float(np.mean(th ** 2))))

@@ -189,6 +189,12 @@ template <typename T> static gp_status adjoint_impl(gp_plan* p, int field, const
   cpx<T>* S = (cpx<T>*)p->adj_ws;
   cpx<T>* tmp = S + (size_t)nsteps * npts;
   const double dt = F.prm.dt, h = 0.5 * dt, shift = F.prm.nonlin_minus_one ? 1.0 : 0.0;
+  const bool f64 = sizeof(T) == 8;
+  const cpx<T>* kd = (const cpx<T>*)ktable(p, field, dt, f64);
+  const cpx<T>* kmd = (const cpx<T>*)ktable(p, field, -dt, f64);
+  const cpx<T>* kh = (const cpx<T>*)ktable(p, field, h, f64);
+  const cpx<T>* kmh = (const cpx<T>*)ktable(p, field, -h, f64);
+  if (!kd || !kmd || !kh || !kmh) return fail(p, GP_ERR_OOM, "kinetic table allocation");
   // recompute the states at the start of every step of the segment
   GP_CUDA(p, cudaMemcpyAsync(S, psi_n, fb, cudaMemcpyDeviceToDevice, s));
   for (int m = 1; m < nsteps; ++m) {
@@ -201,15 +207,15 @@ template <typename T> static gp_status adjoint_impl(gp_plan* p, int field, const
     GP_CUDA(p, cudaMemcpyAsync(tmp, Sm, fb, cudaMemcpyDeviceToDevice, s));
     if (F.prm.split == GP_SPLIT_NKN) {
       GP_CUDA(p, launch_nonlinear<T>(tmp, npts, F.beta * h, shift, s));          // a = N(h) S_m
-      GP_CUDA(p, kinetic3<T>(F, tmp, dt, s));                                    // b = K(dt) a
+      GP_CUDA(p, kinetic3<T>(F, tmp, kd, s));                                    // b = K(dt) a
       GP_CUDA(p, launch_vjp_nonlinear<T>(tmp, lam, npts, F.beta * h, shift, s)); // through N(h) at b
-      GP_CUDA(p, kinetic3<T>(F, lam, -dt, s));                                   // through K(dt)
+      GP_CUDA(p, kinetic3<T>(F, lam, kmd, s));                                   // through K(dt)
       GP_CUDA(p, launch_vjp_nonlinear<T>(Sm, lam, npts, F.beta * h, shift, s));  // through N(h) at S_m
     } else {
-      GP_CUDA(p, kinetic3<T>(F, tmp, h, s));                                    // a = K(h) S_m
-      GP_CUDA(p, kinetic3<T>(F, lam, -h, s));                                   // through the last K(h)
+      GP_CUDA(p, kinetic3<T>(F, tmp, kh, s));                                    // a = K(h) S_m
+      GP_CUDA(p, kinetic3<T>(F, lam, kmh, s));                                   // through the last K(h)
       GP_CUDA(p, launch_vjp_nonlinear<T>(tmp, lam, npts, F.beta * dt, shift, s));// through N(dt) at a
-      GP_CUDA(p, kinetic3<T>(F, lam, -h, s));                                   // through the first K(h)
+      GP_CUDA(p, kinetic3<T>(F, lam, kmh, s));                                   // through the first K(h)
     }
   }
   return GP_OK;

@@ -97,6 +97,25 @@ __device__ __forceinline__ float2 twmul(float2 a, float4 w) {   // a * (w.hi + w
 }
 __device__ __forceinline__ double2 twmul(double2 a, double2 w) { return cmul(a, w); }
 
+// v * w / |w| for a float unit-ish w = c + i s.  |w|^2 - 1 is formed exactly (error-free
+// products; the subtraction is exact by Sterbenz's lemma) and the product uses
+// w (1 - e/2) as a hi + lo pair, so |result| = |v| (1 + O(e^2)) up to one unbiased rounding.
+// A rounded w would scale |v| by the same factor at every step (for the kinetic factor, which
+// is the same for a given k in every step) and make the conserved mass drift.
+__device__ __forceinline__ float2 unit_rotate(float2 v, float c, float s) {
+  const float pc = c * c, ec = fmaf(c, c, -pc);
+  const float ps = s * s, es = fmaf(s, s, -ps);
+  const float big = fmaxf(pc, ps), small = fminf(pc, ps);
+  const float t = (big >= 0.5f) ? ((big - 1.0f) + small) : ((pc - 0.5f) + (ps - 0.5f));
+  const float h = -0.5f * (t + (ec + es));
+  const float dc = c * h, ds = s * h;
+  const float re = fmaf(v.x, c, fmaf(-v.y, s, v.x * dc - v.y * ds));
+  const float im = fmaf(v.x, s, fmaf(v.y, c, v.x * ds + v.y * dc));
+  return float2{re, im};
+}
+__device__ __forceinline__ double2 unit_rotate(double2 v, double c, double s) { return cmul(v, double2{c, s}); }
+
+
 // ---------------------------------------------------------------- butterflies
 // In-register DFTs of size 2, 3, 4, 8, 16, natural order in and out.
 template <bool INV, typename V> __device__ __forceinline__ void dft2(V& a, V& b) {
@@ -214,7 +233,9 @@ template <int L, bool INV> __host__ __device__ constexpr int tw_size() { return 
 // ---------------------------------------------------------------- pencil engine
 // Layout functor Lay: int smem_index(int pencil, int pos).  Registers v[E]:
 // at the input of pass i (radix R) v[b R + r] holds x[t + b TP + r L/R].
-template <typename T, int L, int B, class Lay, bool INV, int I>
+// TW_SH: the twiddle table has been copied to shared memory (plain loads), else read through
+// the read-only data cache.
+template <typename T, int L, int B, class Lay, bool INV, int I, bool TW_SH = false>
 __device__ __forceinline__ void pass_compute(cpx<T>* v, int t, const tw_t<T>* __restrict__ tw) {
   constexpr int R = radix_of<L, INV>(I);
   constexpr int NS = span_of<L, INV>(I);
@@ -228,7 +249,9 @@ __device__ __forceinline__ void pass_compute(cpx<T>* v, int t, const tw_t<T>* __
       const int jm = j % NS;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        v[b * R + r] = twmul(v[b * R + r], __ldg(tw + OFF + jm * (R - 1) + (r - 1)));
+        const tw_t<T>* q = tw + OFF + jm * (R - 1) + (r - 1);
+        if constexpr (TW_SH) v[b * R + r] = twmul(v[b * R + r], *q);
+        else v[b * R + r] = twmul(v[b * R + r], __ldg(q));
       }
     }
   }
@@ -282,25 +305,31 @@ template <int L, bool INV> __device__ __forceinline__ int out_pos(int e, int t) 
 }
 
 // Full 1D transform of the registers: input pattern in_pos<INV>, output pattern out_pos<INV>.
-// Uses shared memory for the exchanges between passes (two barriers each).
-template <typename T, int L, int B, class Lay, bool INV>
+// Uses shared memory for the exchanges between passes (two barriers each).  WARP_X: every
+// pencil's threads lie in one warp and its exchange region is private to it, so the
+// exchanges only need warp-level barriers.
+template <bool WARP_X> __device__ __forceinline__ void xsync() {
+  if constexpr (WARP_X) __syncwarp();
+  else __syncthreads();
+}
+template <typename T, int L, int B, class Lay, bool INV, bool WARP_X = false, bool TW_SH = false>
 __device__ __forceinline__ void fft_regs(cpx<T>* v, int t, int p, cpx<T>* sm, const Lay& lay,
                                          const tw_t<T>* __restrict__ tw) {
   constexpr int NP = Plan<L>::NP;
-  pass_compute<T, L, B, Lay, INV, 0>(v, t, tw);
+  pass_compute<T, L, B, Lay, INV, 0, TW_SH>(v, t, tw);
   if constexpr (NP > 1) {
     pass_store<T, L, Lay, INV, 0>(v, t, p, sm, lay);
-    __syncthreads();
+    xsync<WARP_X>();
     pass_load<T, L, Lay, INV, 1>(v, t, p, sm, lay);
-    __syncthreads();
-    pass_compute<T, L, B, Lay, INV, 1>(v, t, tw);
+    xsync<WARP_X>();
+    pass_compute<T, L, B, Lay, INV, 1, TW_SH>(v, t, tw);
   }
   if constexpr (NP > 2) {
     pass_store<T, L, Lay, INV, 1>(v, t, p, sm, lay);
-    __syncthreads();
+    xsync<WARP_X>();
     pass_load<T, L, Lay, INV, 2>(v, t, p, sm, lay);
-    __syncthreads();
-    pass_compute<T, L, B, Lay, INV, 2>(v, t, tw);
+    xsync<WARP_X>();
+    pass_compute<T, L, B, Lay, INV, 2, TW_SH>(v, t, tw);
   }
 }
 

@@ -1,5 +1,6 @@
 // Instantiations of the pencil sweeps for some grid lengths (compiled in parallel).
 #include "gp_internal.h"
+#include "gp_tma.cuh"
 
 namespace gp {
 cudaError_t sweep_f32_64(const SweepArgs<float>& a, cudaStream_t s) { return SweepLaunch<float, 64>::launch(a, s); }
@@ -10,4 +11,10 @@ cudaError_t sweep_f32_128(const SweepArgs<float>& a, cudaStream_t s) { return Sw
 cudaError_t sweep_f64_128(const SweepArgs<double>& a, cudaStream_t s) { return SweepLaunch<double, 128>::launch(a, s); }
 cudaError_t sweep_f32_192(const SweepArgs<float>& a, cudaStream_t s) { return SweepLaunch<float, 192>::launch(a, s); }
 cudaError_t sweep_f64_192(const SweepArgs<double>& a, cudaStream_t s) { return SweepLaunch<double, 192>::launch(a, s); }
+cudaError_t tma_sweep_32(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<32>::launch(a, ctas, s); }
+cudaError_t tma_sweep_48(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<48>::launch(a, ctas, s); }
+cudaError_t tma_sweep_64(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<64>::launch(a, ctas, s); }
+cudaError_t tma_sweep_96(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<96>::launch(a, ctas, s); }
+cudaError_t tma_sweep_128(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<128>::launch(a, ctas, s); }
+cudaError_t tma_sweep_192(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<192>::launch(a, ctas, s); }
 }  // namespace gp

@@ -16,7 +16,17 @@ namespace gp {
 GP_SIZES(GP_DECL_SWEEP)
 #undef GP_DECL_SWEEP
 
+#define GP_TMA_SIZES(X) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512) X(1024)
+struct TmaSweepArgs;
+#define GP_DECL_TMA(L) cudaError_t tma_sweep_##L(const TmaSweepArgs&, int, cudaStream_t);
+GP_TMA_SIZES(GP_DECL_TMA)
+#undef GP_DECL_TMA
+bool tma_supported(int n);
+// launch one TMA sweep for the fields psi[0..count) of length n (float32 fused path)
+cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* status, cudaStream_t s);
+
 bool supported_n(int n);
+void split_hilo(double v, float* hi, float* lo);   // see gp_plan.cu
 int plan_np(int n);           // number of radix passes for length n
 int plan_radix_fwd(int n, int i);
 cudaError_t sweep(int n, const SweepArgs<float>& a, cudaStream_t s);
@@ -61,6 +71,7 @@ struct gp_plan {
   std::vector<void*> cycle_key;            // field pointers the graph was captured for
   int cycle_len = 0;
   long long launches = 0;                  // kernels launched or replayed
+  bool use_tma = true;                     // float32 sweeps through the TMA-pipelined kernels
   bool prof = false;                       // per-launch event timing (gp_profile)
   std::vector<cudaEvent_t> ev_pool;        // recorded events, two per profiled launch
   std::vector<int> ev_kind;                // kind index of each profiled launch
@@ -82,8 +93,8 @@ gp_status ensure_ws(gp_plan* p, int field, size_t bytes);
 
 // 3D transforms of a whole field through the pencil sweeps (unfused).
 template <typename T> cudaError_t fft3(FieldPlan& F, cpx<T>* x, bool inverse, cudaStream_t s);
-// K(s_k) with fused sweeps: fwd z, fwd y, [fwd x, K, 1/N^3, inv x], inv y, inv z.
-template <typename T> cudaError_t kinetic3(FieldPlan& F, cpx<T>* x, double s_k, cudaStream_t s);
+// K with fused sweeps: fwd z, fwd y, [fwd x, K (table ek), 1/N^3, inv x], inv y, inv z.
+template <typename T> cudaError_t kinetic3(FieldPlan& F, cpx<T>* x, const cpx<T>* ek, cudaStream_t s);
 template <typename T> const Tables& tables(FieldPlan& F);
 
 // pointwise kernels (gp_pointwise.cu)

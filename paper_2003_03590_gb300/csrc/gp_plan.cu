@@ -1,6 +1,7 @@
 // gp_plan.cu -- plan object, float64-generated tables, dispatch and error handling of the C ABI.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -87,13 +88,36 @@ static void twiddles(int n, bool inv, std::vector<double>& re, std::vector<doubl
   }
 }
 
+// v = hi + lo, hi = v rounded to 12 significant bits, lo = the float remainder (hi + lo = v to
+// about 2^-36).  The compensated multiply fma(a, c_hi, fma(b, s_hi, lo_terms)) rounds twice; its
+// inner rounding must not depend on the value of hi in a fixed way.  With a full-precision hi a
+// product a*hi can be exact (hi = 1/2, the 30-degree twiddles of radix-3 lengths) or sit on a
+// rounding midpoint (hi = 0.49999997 = 1/2 - 2^-25), and the lo terms are then rounded away with
+// the same sign at every step, which makes the conserved mass drift.  A 12-bit hi leaves at least
+// 12 bits of every product below the float32 ulp, set by the datum's low bits: unbiased rounding.
+void split_hilo(double v, float* hi, float* lo) {
+  if (v == 0.0) {
+    *hi = 0.0f;
+    *lo = 0.0f;
+    return;
+  }
+  int e = 0;
+  const double m = std::frexp(v, &e);                    // v = m 2^e, 1/2 <= |m| < 1
+  const double h = std::ldexp(std::nearbyint(m * 4096.0) / 4096.0, e);
+  *hi = (float)h;
+  *lo = (float)(v - h);
+}
+
 template <typename V> static V pack(double c, double s);
 // float32 twiddles keep the rounded value and the remainder, (hi.x, hi.y, lo.x, lo.y)
 template <> float4 pack<float4>(double c, double s) {
-  const float ch = (float)c, sh = (float)s;
-  return make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
+  float ch, cl, sh, sl;
+  split_hilo(c, &ch, &cl);
+  split_hilo(s, &sh, &sl);
+  return make_float4(ch, sh, cl, sl);
 }
 template <> double2 pack<double2>(double c, double s) { return make_double2(c, s); }
+template <> float2 pack<float2>(double c, double s) { return make_float2((float)c, (float)s); }
 
 template <typename V> static cudaError_t upload(const std::vector<double>& re, const std::vector<double>& im, void** dev) {
   std::vector<V> h(re.size() > 0 ? re.size() : 1);
@@ -129,6 +153,9 @@ static void ktable_values(int n, double alpha, double s, std::vector<double>& re
   }
 }
 
+// float64 fields: N entries exp(-i alpha k^2 s).  float32 fields: N hi/lo entries of the same,
+// followed by N^2 hi/lo entries of exp(-i alpha (k1^2 + k2^2) s) / N^3 (index i2 N + i1),
+// each formed in float64 and split into hi + lo.
 const void* ktable(gp_plan* p, int field, double s, bool fp64) {
   FieldPlan& F = p->f[field];
   std::vector<KTable>& cache = fp64 ? F.k64 : F.k32;
@@ -138,7 +165,25 @@ const void* ktable(gp_plan* p, int field, double s, bool fp64) {
   ktable_values(F.n, F.alpha, s, re, im);
   KTable kt;
   kt.s = s;
-  cudaError_t e = fp64 ? upload<double2>(re, im, &kt.dev) : upload<float4>(re, im, &kt.dev);
+  cudaError_t e;
+  if (fp64) {
+    e = upload<double2>(re, im, &kt.dev);
+  } else {
+    const int n = F.n;
+    const double norm = 1.0 / (double)F.npts;
+    std::vector<double> r2((size_t)n + (size_t)n * n), i2((size_t)n + (size_t)n * n);
+    for (int i = 0; i < n; ++i) {
+      r2[i] = re[i];
+      i2[i] = im[i];
+    }
+    for (int b = 0; b < n; ++b)
+      for (int a = 0; a < n; ++a) {
+        const size_t q = (size_t)n + (size_t)b * n + a;
+        r2[q] = (re[a] * re[b] - im[a] * im[b]) * norm;
+        i2[q] = (re[a] * im[b] + im[a] * re[b]) * norm;
+      }
+    e = upload<float4>(r2, i2, &kt.dev);
+  }
   if (e != cudaSuccess) return nullptr;
   cache.push_back(kt);
   return kt.dev;
@@ -179,15 +224,20 @@ template <typename T> cudaError_t fft3(FieldPlan& F, cpx<T>* x, bool inverse, cu
 template cudaError_t fft3<float>(FieldPlan&, cpx<float>*, bool, cudaStream_t);
 template cudaError_t fft3<double>(FieldPlan&, cpx<double>*, bool, cudaStream_t);
 
-template <typename T> cudaError_t kinetic3(FieldPlan& F, cpx<T>* x, double s_k, cudaStream_t s) {
+template <typename T> cudaError_t kinetic3(FieldPlan& F, cpx<T>* x, const cpx<T>* ek, cudaStream_t s) {
   const Tables& tb = tables<T>(F);
   SweepArgs<T> a{};
   a.psi[0] = x;
   a.count = 1;
   a.tw_fwd = (const tw_t<T>*)tb.tw_fwd;
   a.tw_inv = (const tw_t<T>*)tb.tw_inv;
-  a.k_coef = kconst(F.alpha * s_k);
-  a.k_norm = kconst(1.0 / (double)F.npts);
+  if constexpr (sizeof(T) == 4) {
+    a.ekx = (const float4*)ek;
+    a.ek2 = (const float4*)ek + F.n;
+  } else {
+    a.ek = ek;
+    a.k_norm = kconst(1.0 / (double)F.npts);
+  }
   a.scale_inv = 0;
   const int axes[5] = {2, 1, 0, 1, 2};
   const int ops[5] = {OP_FWD, OP_FWD, OP_FWD_K_INV, OP_INV, OP_INV};
@@ -199,8 +249,8 @@ template <typename T> cudaError_t kinetic3(FieldPlan& F, cpx<T>* x, double s_k, 
   }
   return cudaSuccess;
 }
-template cudaError_t kinetic3<float>(FieldPlan&, cpx<float>*, double, cudaStream_t);
-template cudaError_t kinetic3<double>(FieldPlan&, cpx<double>*, double, cudaStream_t);
+template cudaError_t kinetic3<float>(FieldPlan&, cpx<float>*, const cpx<float>*, cudaStream_t);
+template cudaError_t kinetic3<double>(FieldPlan&, cpx<double>*, const cpx<double>*, cudaStream_t);
 
 static void free_field(FieldPlan& F) {
   void* ptrs[] = {F.t32.tw_fwd, F.t32.tw_inv, F.t64.tw_fwd, F.t64.tw_inv, F.host_buf, F.ws};
@@ -249,6 +299,9 @@ gp_status gp_plan_create(const gp_field_params* fields, int nfields, void* strea
   }
   gp_plan* p = new gp_plan();
   p->stream = (cudaStream_t)stream;
+  // GP_SWEEPS=plain selects the non-TMA float32 sweep kernels (for comparisons)
+  const char* env = std::getenv("GP_SWEEPS");
+  p->use_tma = !(env && std::strcmp(env, "plain") == 0);
   p->f.resize(nfields);
   for (int i = 0; i < nfields; ++i) {
     FieldPlan& F = p->f[i];

@@ -80,13 +80,19 @@ gp_status launch_item(gp_plan* p, const Group& G, const Item& it, void* const* p
   a.axis = it.axis;
   a.nl_coef = (float)(F.beta * it.s_nl);
   a.nl_shift = F.prm.nonlin_minus_one ? 1.0f : 0.0f;
-  a.k_coef = kconst(F.alpha * it.s_k);
-  a.k_norm = kconst(1.0 / (double)F.npts);   // the whole inverse normalisation, applied with K
+  if (it.op == OP_FWD_K_INV) {
+    const float4* kt = (const float4*)ktable(p, G.fields[0], it.s_k, false);
+    if (!kt) return fail(p, GP_ERR_OOM, "kinetic table allocation");
+    a.ekx = kt;
+    a.ek2 = kt + G.n;   // includes the whole inverse normalisation 1/N^3
+  }
   a.scale_inv = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (p->prof) {
     static const char* opn[] = {"", "fwd", "inv", "inv_n_fwd", "n_fwd", "inv_n", "fwd_k_inv"};
-    std::string name = std::string(it.axis == 0 ? "k_sweep_contig<float," : "k_sweep_strided<float,") +
+    const bool tma = p->use_tma && tma_supported(G.n);
+    std::string name = std::string(tma ? (it.axis == 0 ? "k_tma_contig<" : "k_tma_strided<")
+                                       : (it.axis == 0 ? "k_sweep_contig<float," : "k_sweep_strided<float,")) +
                        std::to_string(G.n) + ">:" + opn[it.op] + ":" + "xyz"[it.axis];
     int kind = -1;
     for (int q = 0; q < (int)p->kinds.size(); ++q)
@@ -102,7 +108,14 @@ gp_status launch_item(gp_plan* p, const Group& G, const Item& it, void* const* p
     p->ev_pool.push_back(e1);
     p->ev_kind.push_back(kind);
   }
-  cudaError_t e = sweep(G.n, a, s);
+  cudaError_t e;
+  if (p->use_tma && tma_supported(G.n)) {
+    void* ptrs[GP_MAXB];
+    for (int k = 0; k < a.count; ++k) ptrs[k] = psi[G.fields[k]];
+    e = tma_sweep(G.n, a, ptrs, p->flag + 1, s);
+  } else {
+    e = sweep(G.n, a, s);
+  }
   if (e != cudaSuccess) return cuda_fail(p, e, "sweep launch");
   if (p->prof) GP_CUDA(p, cudaEventRecord(e1, s));
   p->launches += 1;
@@ -174,6 +187,10 @@ gp_status step_all(gp_plan* p, void* const* psi, int nsteps) {
       continue;
     }
     any32 = true;
+    // tables are created before any capture starts
+    const FieldPlan& F = p->f[G.fields[0]];
+    if (!ktable(p, G.fields[0], F.prm.dt, false) || !ktable(p, G.fields[0], 0.5 * F.prm.dt, false))
+      return fail(p, GP_ERR_OOM, "kinetic table allocation");
   }
   if (!any32) return GP_OK;
 

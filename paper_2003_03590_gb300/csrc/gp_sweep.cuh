@@ -11,10 +11,9 @@
 //                 Fourier space), inverse DFT
 // N(s):  psi <- exp(-i (beta s) (|psi|^2 - c)) psi                 (exact nonlinear flow)
 // K(s):  psi_k <- exp(-i alpha s (kx^2 + ky^2 + kz^2)) psi_k          (exact kinetic flows)
-// The kinetic phase is formed per element from the integer |k|^2 and evaluated
-// with sincos, so its rounding is unbiased; the 1/N^3 of the inverse transform
-// is folded into the same multiplication (the inverse sweeps that follow it in a
-// step then do not scale).
+// The kinetic factor is applied with an exact magnitude (unit_rotate) and the 1/N^3
+// of the inverse transform is folded into the same multiplication (the inverse
+// sweeps that follow it in a step then do not scale).
 #pragma once
 #include "gp_fft.cuh"
 
@@ -29,8 +28,10 @@ template <typename T> struct SweepArgs {
   int count;                // number of fields in psi[]
   const tw_t<T>* tw_fwd;    // forward Stockham twiddles for length N
   const tw_t<T>* tw_inv;    // inverse Stockham twiddles for length N
-  KConst k_coef;            // alpha * s of K(s) (OP_FWD_K_INV)
-  KConst k_norm;            // factor applied with K: 1/N^3 (fused step) or 1
+  const cpx<T>* ek;         // float64: exp(-i alpha s k^2) by grid index, length N (OP_FWD_K_INV)
+  const float4* ekx;        // float32: the same as hi/lo pairs, length N
+  const float4* ek2;        // float32: E[i1] E[i2] / N^3 as hi/lo pairs, index i2 * N + i1
+  KConst k_norm;            // float64: factor applied with K, 1/N^3
   T nl_coef;                // beta * s of N(s)
   T nl_shift;               // c of N(s): 1 (eq-gpe-num) or 0
   int op;
@@ -38,26 +39,10 @@ template <typename T> struct SweepArgs {
   int scale_inv;            // 1: inverse ops multiply by 1/N; 0: normalisation done with K
 };
 
-template <int L> __device__ __forceinline__ int ksq(int i) {   // squared integer wavenumber of index i
-  const int k = i < (L + 1) / 2 ? i : i - L;
-  return k * k;
-}
-
-// exp(-i coef k2) x, the phase formed from the exact integer k2
-template <typename V> __device__ __forceinline__ V kinetic_phase(V x, KConst coef, KConst norm, int k2) {
-  if constexpr (sizeof(x.x) == 4) {
-    const float kf = (float)k2;
-    const float ph = fmaf(coef.hi, kf, coef.lo * kf);
-    float sn, cs;
-    sincosf(ph, &sn, &cs);
-    V y{x.x * cs + x.y * sn, x.y * cs - x.x * sn};
-    return V{kmul(y.x, norm), kmul(y.y, norm)};
-  } else {
-    double sn, cs;
-    sincos(coef.v * (double)k2, &sn, &cs);
-    V y{x.x * cs + x.y * sn, x.y * cs - x.x * sn};
-    return V{y.x * norm.v, y.y * norm.v};
-  }
+// K factor of one element (float64): E[kx] (E[ky] E[kz]) from the table of exp(-i alpha s k^2), then 1/N^3.
+__device__ __forceinline__ double2 kinetic_apply(double2 x, double2 e_other, double2 e_pos, KConst norm) {
+  const double2 y = cmul(x, cmul(e_pos, e_other));
+  return double2{y.x * norm.v, y.y * norm.v};
 }
 
 template <typename V> __device__ __forceinline__ V kscale(V x, KConst k) { return V{kmul(x.x, k), kmul(x.y, k)}; }
@@ -84,13 +69,35 @@ template <int L> struct LayContig {  // [pencil][pos] with one pad element every
   }
 };
 
+// cos(x) - 1 and sin(x) for |x| <= 1/2 by their Taylor series (terms to x^10 and x^9; the first
+// omitted term is below 2e-11).  cos(x) - 1 keeps full relative precision for small x: rounding
+// cos(x) itself to float would give exactly 1 for |x| < 2.4e-4 and |w|^2 = 1 + x^2, a bias.
+__device__ __forceinline__ void sincos_m1_small(float x, float* s, float* cm1) {
+  const float z = x * x;
+  const float pc = fmaf(z, fmaf(z, fmaf(z, fmaf(z, -2.7557319e-7f, 2.4801587e-5f), -1.3888889e-3f), 4.1666668e-2f), -0.5f);
+  *cm1 = z * pc;
+  const float ps = fmaf(z, fmaf(z, fmaf(z, 2.7557319e-6f, -1.9841270e-4f), 8.3333333e-3f), -0.16666667f);
+  *s = fmaf(x * z, ps, x);
+}
+
+// N(s): a * exp(-i coef (|a|^2 - shift)).  For a small phase the product is formed as
+// a + a (cos - 1 - i sin), so its roundings act on the result only and stay unbiased.
 template <typename V, typename S> __device__ __forceinline__ V nonlinear(V a, S coef, S shift) {
   S r2 = a.x * a.x + a.y * a.y;
   S ph = coef * (r2 - shift);
   S sn, cs;
-  if constexpr (sizeof(S) == 4) sincosf(ph, &sn, &cs);
-  else sincos(ph, &sn, &cs);
-  return V{a.x * cs + a.y * sn, a.y * cs - a.x * sn};  // a * exp(-i ph)
+  if constexpr (sizeof(S) == 4) {
+    if (fabsf(ph) <= 0.5f) {
+      float cm1;
+      sincos_m1_small(ph, &sn, &cm1);
+      return V{fmaf(a.x, cm1, fmaf(a.y, sn, a.x)), fmaf(a.y, cm1, fmaf(-a.x, sn, a.y))};
+    }
+    sincosf(ph, &sn, &cs);
+    return unit_rotate(a, cs, -sn);
+  } else {
+    sincos(ph, &sn, &cs);
+    return V{a.x * cs + a.y * sn, a.y * cs - a.x * sn};
+  }
 }
 
 template <typename T, int L, bool INV, class GetAddr>
@@ -106,11 +113,15 @@ __device__ __forceinline__ void store_pattern(const cpx<T>* v, int t, const GetA
   for (int e = 0; e < E; ++e) *addr(out_pos<L, INV>(e, t)) = v[e];
 }
 
-// Body shared by both tile shapes.  k2o is the sum of the squared wavenumbers of the
-// pencil's two other coordinates (only used by OP_FWD_K_INV).
-template <typename T, int L, int B, class Lay, class GetAddr>
+// Body shared by both tile shapes.  (i1, i2) are the grid indices of the pencil's two other
+// coordinates (only used by OP_FWD_K_INV).
+// TILE_IN_SMEM: the tile addressed by addr() lives in the same shared memory that the
+// passes use for their exchanges, so the block synchronises after reading it (and, with
+// warp-private exchanges, before writing it back).  WARP_X: see fft_regs.
+template <typename T, int L, int B, class Lay, class GetAddr, bool TILE_IN_SMEM = false, bool WARP_X = false,
+          bool TW_SH = false>
 __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a, int t, int p, cpx<T>* sm, const Lay& lay,
-                                           const GetAddr& addr, int k2o) {
+                                           const GetAddr& addr, int i1, int i2) {
   using V = cpx<T>;
   constexpr int E = Plan<L>::E;
   constexpr KConst inv_l = kconst(1.0 / L);
@@ -119,48 +130,71 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a, int t, int p, 
   switch (a.op) {
     case OP_FWD:
       load_pattern<T, L, false>(v, t, addr);
-      fft_regs<T, L, B, Lay, false>(v, t, p, sm, lay, a.tw_fwd);
+      if constexpr (TILE_IN_SMEM) __syncthreads();
+      fft_regs<T, L, B, Lay, false, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_fwd);
+      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
       store_pattern<T, L, false>(v, t, addr);
       break;
     case OP_INV:
       load_pattern<T, L, true>(v, t, addr);
-      fft_regs<T, L, B, Lay, true>(v, t, p, sm, lay, a.tw_inv);
+      if constexpr (TILE_IN_SMEM) __syncthreads();
+      fft_regs<T, L, B, Lay, true, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_inv);
       if (sc) {
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = kscale(v[e], inv_l);
       }
+      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
       store_pattern<T, L, true>(v, t, addr);
       break;
     case OP_N_FWD:
       load_pattern<T, L, false>(v, t, addr);
+      if constexpr (TILE_IN_SMEM) __syncthreads();
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = nonlinear(v[e], a.nl_coef, a.nl_shift);
-      fft_regs<T, L, B, Lay, false>(v, t, p, sm, lay, a.tw_fwd);
+      fft_regs<T, L, B, Lay, false, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_fwd);
+      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
       store_pattern<T, L, false>(v, t, addr);
       break;
     case OP_INV_N:
       load_pattern<T, L, true>(v, t, addr);
-      fft_regs<T, L, B, Lay, true>(v, t, p, sm, lay, a.tw_inv);
+      if constexpr (TILE_IN_SMEM) __syncthreads();
+      fft_regs<T, L, B, Lay, true, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_inv);
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = nonlinear(sc ? kscale(v[e], inv_l) : v[e], a.nl_coef, a.nl_shift);
+      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
       store_pattern<T, L, true>(v, t, addr);
       break;
     case OP_INV_N_FWD:
       load_pattern<T, L, true>(v, t, addr);
-      fft_regs<T, L, B, Lay, true>(v, t, p, sm, lay, a.tw_inv);
+      if constexpr (TILE_IN_SMEM) __syncthreads();
+      fft_regs<T, L, B, Lay, true, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_inv);
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = nonlinear(sc ? kscale(v[e], inv_l) : v[e], a.nl_coef, a.nl_shift);
-      __syncthreads();  // shared memory is reused by the forward passes
-      fft_regs<T, L, B, Lay, false>(v, t, p, sm, lay, a.tw_fwd);
+      xsync<WARP_X>();  // shared memory is reused by the forward passes
+      fft_regs<T, L, B, Lay, false, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_fwd);
+      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
       store_pattern<T, L, false>(v, t, addr);
       break;
     case OP_FWD_K_INV:
       load_pattern<T, L, false>(v, t, addr);
-      fft_regs<T, L, B, Lay, false>(v, t, p, sm, lay, a.tw_fwd);
+      if constexpr (TILE_IN_SMEM) __syncthreads();
+      fft_regs<T, L, B, Lay, false, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_fwd);
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = kinetic_phase(v[e], a.k_coef, a.k_norm, k2o + ksq<L>(out_pos<L, false>(e, t)));
-      __syncthreads();
-      fft_regs<T, L, B, Lay, true>(v, t, p, sm, lay, a.tw_inv);
+      if constexpr (sizeof(T) == 4) {
+        // two products by factors exact to float64 (hi + lo), each rounded once: the magnitude
+        // of the field is not biased by the kinetic factor, which is the same for a given k in
+        // every step
+        const float4 eo = __ldg(a.ek2 + i2 * L + i1);
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = twmul(twmul(v[e], __ldg(a.ekx + out_pos<L, false>(e, t))), eo);
+      } else {
+        const V eo = cmul(__ldg(a.ek + i1), __ldg(a.ek + i2));
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = kinetic_apply(v[e], eo, __ldg(a.ek + out_pos<L, false>(e, t)), a.k_norm);
+      }
+      xsync<WARP_X>();
+      fft_regs<T, L, B, Lay, true, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_inv);
+      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
       store_pattern<T, L, true>(v, t, addr);
       break;
     default:
@@ -184,7 +218,7 @@ __global__ void __launch_bounds__(strided_batch<T, L>() * (L / Plan<L>::E))
   V* base = a.psi[blockIdx.y] + x0 + p + (long)c * sc;
   auto addr = [&](int pos) { return base + (long)pos * st; };
   LayStrided lay{B};
-  sweep_body<T, L, B>(a, t, p, sm, lay, addr, ksq<L>(x0 + p) + ksq<L>(c));
+  sweep_body<T, L, B>(a, t, p, sm, lay, addr, x0 + p, c);
 }
 
 // x rows: a CTA owns B consecutive rows (y, z).
@@ -200,7 +234,8 @@ __global__ void __launch_bounds__(contig_batch<T, L>() * (L / Plan<L>::E)) k_swe
   V* base = a.psi[blockIdx.y] + row * L;
   auto addr = [&](int pos) { return base + pos; };
   LayContig<L> lay;
-  sweep_body<T, L, B>(a, t, p, sm, lay, addr, ksq<L>((int)(row % L)) + ksq<L>((int)(row / L)));
+  sweep_body<T, L, B, LayContig<L>, decltype(addr), false, (TP <= 32)>(a, t, p, sm, lay, addr, (int)(row % L),
+                                                                        (int)(row / L));
 }
 
 template <typename T, int L> struct SweepLaunch {

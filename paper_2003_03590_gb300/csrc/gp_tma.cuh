@@ -1,0 +1,350 @@
+// gp_tma.cuh -- persistent, TMA-pipelined float32 sweeps.
+//
+// Each CTA walks a list of tiles (a tile = B pencils of one axis).  Tiles move between
+// HBM and a ring of S shared-memory stages with tensor-memory-accelerator bulk copies
+// (cp.async.bulk.tensor, completion on an mbarrier for loads, bulk groups for stores),
+// so loads of later tiles and stores of earlier ones overlap the FFT arithmetic of the
+// current tile.  The arithmetic is the register Stockham engine of gp_fft.cuh with the
+// pointwise flows of gp_sweep.cuh; only the data movement differs from k_sweep_*.
+//
+// Every wait on an mbarrier is bounded: if a copy does not complete within the bound the
+// CTA records the failure in a device status word and returns after waiting (again
+// bounded) for its own outstanding copies.
+#pragma once
+#include <cuda.h>
+
+#include "gp_sweep.cuh"
+
+namespace gp {
+
+struct TmaSweepArgs {
+  CUtensorMap map[GP_MAXB];   // one 3D map per field ([z][y][x], 8-byte elements)
+  int count;                  // fields
+  const tw_t<float>* tw_fwd;
+  const tw_t<float>* tw_inv;
+  const float4* ekx;
+  const float4* ek2;
+  float nl_coef, nl_shift;
+  int op, axis, scale_inv;
+  int* status;                // set to 1 when a bounded wait gives up
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false if the phase did not complete within the iteration limit
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(map),
+               "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// tile geometry of the strided (y, z) sweeps: B pencils of length L, boxes of at most 256 along the pencil.
+// L <= 256 ("swizzled" tiles): the B = 16 pencils of a tile are 128-byte rows of the box; TMA
+// stores them with the 128-byte swizzle (16-byte chunk c of row r lands at chunk c ^ (r mod 8)),
+// which lets a thread walk one pencil (a column of the tile) with 2-way instead of 16-way bank
+// conflicts; each pencil then belongs to one warp and its exchanges use a private padded region.
+#ifndef GP_TMA_SWIZZLE
+#define GP_TMA_SWIZZLE 0   // measured slower on GB300 than the [pos][pencil] layout with block-wide exchanges
+#endif
+template <int L> struct TmaStrided {
+  static constexpr bool SWZ = GP_TMA_SWIZZLE && L <= 256;
+  static constexpr int B = L >= 1024 ? 4 : (L >= 512 ? 8 : 16);
+  static constexpr int TP = L / Plan<L>::E;
+  static constexpr int NT = B * TP;
+  static constexpr int TILE = B * L;                       // elements
+  static constexpr int EXCH = SWZ ? B * contig_pitch<L>() : TILE;
+  static constexpr int STAGE = ((((TILE > EXCH ? TILE : EXCH) * 8) + 1023) / 1024) * 128;   // elements, 1 KB multiple
+  static constexpr int BOX = L > 256 ? 256 : L;            // pencil extent of one box
+  static constexpr int NBOX = L / BOX;
+  static constexpr int S = 3;                              // stages
+  static constexpr bool TWS = L <= 256;                    // twiddles in shared memory
+  static constexpr int TWF = tw_size<L, false>(), TWI = tw_size<L, true>();
+  static constexpr size_t TWB = TWS ? (size_t)(TWF + TWI) * 16 : 0;
+  static constexpr size_t SMEM = (size_t)S * STAGE * 8 + 64 + TWB + 1024;   // + alignment slack
+};
+// element index of tile element i after the 128-byte swizzle (byte bits 7..9 XOR into bits 4..6)
+__device__ __forceinline__ int swz128(int i) { return i ^ (((i >> 4) & 7) << 1); }
+// x rows: B rows of length L; boxes of at most 256 along x; stage sized for the padded exchange layout
+template <int L> struct TmaContig {
+  static constexpr int TP = L / Plan<L>::E;
+  static constexpr int B = (256 / TP) < 1 ? 1 : ((256 / TP) > 16 ? 16 : 256 / TP);
+  static constexpr int NT = B * TP;
+  static constexpr int TILE = B * L;
+  static constexpr int STAGE = B * contig_pitch<L>();     // elements, >= TILE
+  static constexpr int BOX = L > 256 ? 256 : L;
+  static constexpr int NBOX = L / BOX;
+  static constexpr int S = 3;
+  static constexpr bool TWS = L <= 256;
+  static constexpr int TWF = tw_size<L, false>(), TWI = tw_size<L, true>();
+  static constexpr size_t TWB = TWS ? (size_t)(TWF + TWI) * 16 : 0;
+  static constexpr size_t SMEM = (size_t)S * STAGE * 8 + 64 + TWB;
+};
+
+// y or z pencils; tile index -> (field, x0, c), c the other coordinate (z for y pencils, y for z)
+template <int L>
+__global__ void __launch_bounds__(TmaStrided<L>::NT) k_tma_strided(const __grid_constant__ TmaSweepArgs a) {
+  using G = TmaStrided<L>;
+  using V = float2;
+  constexpr int B = G::B, S = G::S, TILE = G::TILE, STAGE = G::STAGE, TP = G::TP;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  // stages start on a 1 KB boundary of the shared window (the swizzle pattern is absolute)
+  const uint32_t base = smem_u32(smraw);
+  V* buf = reinterpret_cast<V*>(smraw + (((base + 1023u) & ~1023u) - base));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(buf + (size_t)S * STAGE);
+  const int tid = threadIdx.x;
+  const int p = G::SWZ ? tid / TP : tid % B, t = G::SWZ ? tid % TP : tid / B;
+  const int per_field = (L / B) * L;
+  const int total = per_field * a.count;
+  const unsigned bytes = (unsigned)TILE * 8u;
+
+  auto coords = [&](int tile, int& f, int& x0, int& c) {
+    f = tile / per_field;
+    const int r = tile - f * per_field;
+    x0 = (r % (L / B)) * B;
+    c = r / (L / B);
+  };
+  auto issue_load = [&](int tile, int s) {
+    int f, x0, c;
+    coords(tile, f, x0, c);
+    mbar_expect_tx(&bar[s], bytes);
+#pragma unroll
+    for (int k = 0; k < G::NBOX; ++k) {
+      V* dst = buf + (size_t)s * STAGE + (size_t)k * G::BOX * B;
+      if (a.axis == 1) tma_load_3d(dst, &a.map[f], &bar[s], x0, k * G::BOX, c);
+      else tma_load_3d(dst, &a.map[f], &bar[s], x0, c, k * G::BOX);
+    }
+  };
+  auto issue_store = [&](int tile, int s) {
+    int f, x0, c;
+    coords(tile, f, x0, c);
+#pragma unroll
+    for (int k = 0; k < G::NBOX; ++k) {
+      const V* src = buf + (size_t)s * STAGE + (size_t)k * G::BOX * B;
+      if (a.axis == 1) tma_store_3d(&a.map[f], src, x0, k * G::BOX, c);
+      else tma_store_3d(&a.map[f], src, x0, c, k * G::BOX);
+    }
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+    for (int s = 0; s < S; ++s) {
+      const int tile = blockIdx.x + s * gridDim.x;
+      if (tile < total) issue_load(tile, s);
+    }
+  }
+  float4* tws = reinterpret_cast<float4*>(bar + 8);   // 64 bytes of barriers, then the twiddles
+  if constexpr (G::TWS) {
+    for (int i = tid; i < G::TWF; i += blockDim.x) tws[i] = a.tw_fwd[i];
+    for (int i = tid; i < G::TWI; i += blockDim.x) tws[G::TWF + i] = a.tw_inv[i];
+  }
+  __syncthreads();
+
+  SweepArgs<float> sa{};
+  sa.tw_fwd = G::TWS ? tws : a.tw_fwd;
+  sa.tw_inv = G::TWS ? tws + G::TWF : a.tw_inv;
+  sa.ekx = a.ekx;
+  sa.ek2 = a.ek2;
+  sa.nl_coef = a.nl_coef;
+  sa.nl_shift = a.nl_shift;
+  sa.op = a.op;
+  sa.axis = a.axis;
+  sa.scale_inv = a.scale_inv;
+  bool failed = false;
+  int it = 0;
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
+    const int s = it % S;
+    const bool ok = mbar_wait_bounded(&bar[s], (unsigned)(it / S) & 1u);
+    if (!__syncthreads_and(ok)) {   // every thread takes the same decision
+      failed = true;
+      break;
+    }
+    V* sm = buf + (size_t)s * STAGE;
+    int f, x0, c;
+    coords(tile, f, x0, c);
+    if constexpr (G::SWZ) {
+      auto addr = [&](int pos) { return sm + swz128(pos * B + p); };
+      LayContig<L> lay;
+      sweep_body<float, L, B, LayContig<L>, decltype(addr), true, true, G::TWS>(sa, t, p, sm, lay, addr, x0 + p, c);
+    } else {
+      auto addr = [&](int pos) { return sm + pos * B + p; };
+      LayStrided lay{B};
+      sweep_body<float, L, B, LayStrided, decltype(addr), true, false, G::TWS>(sa, t, p, sm, lay, addr, x0 + p, c);
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      issue_store(tile, s);
+      bulk_commit();
+      if (it >= 1) {
+        const int nxt = tile - gridDim.x + S * gridDim.x;   // the tile the previous stage serves next
+        if (nxt < total) {
+          bulk_wait_read1();                                // the previous stage's store has left smem
+          issue_load(nxt, (it - 1) % S);
+        }
+      }
+    }
+  }
+  if (failed) {
+    if (tid == 0) atomicExch(a.status, 1);
+  }
+  if (tid == 0) bulk_wait_all();
+  if (failed && tid == 0) {
+    // let the loads still in flight land before the CTA's shared memory goes away
+    for (int s = 0; s < S; ++s) mbar_wait_bounded(&bar[s], 0u), mbar_wait_bounded(&bar[s], 1u);
+  }
+}
+
+// x rows; tile index -> (field, row0); row = y + N z
+template <int L>
+__global__ void __launch_bounds__(TmaContig<L>::NT) k_tma_contig(const __grid_constant__ TmaSweepArgs a) {
+  using G = TmaContig<L>;
+  using V = float2;
+  constexpr int B = G::B, S = G::S, TILE = G::TILE, STAGE = G::STAGE, TP = G::TP;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  V* buf = reinterpret_cast<V*>(smraw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + (size_t)S * STAGE * 8);
+  const int tid = threadIdx.x, p = tid / TP, t = tid % TP;
+  const int per_field = L * L / B;
+  const int total = per_field * a.count;
+  const unsigned bytes = (unsigned)TILE * 8u;
+
+  auto issue_load = [&](int tile, int s) {
+    const int f = tile / per_field, row0 = (tile - f * per_field) * B;
+    mbar_expect_tx(&bar[s], bytes);
+#pragma unroll
+    for (int k = 0; k < G::NBOX; ++k)
+      tma_load_3d(buf + (size_t)s * STAGE + (size_t)k * G::BOX * B, &a.map[f], &bar[s], k * G::BOX, row0 % L, row0 / L);
+  };
+  auto issue_store = [&](int tile, int s) {
+    const int f = tile / per_field, row0 = (tile - f * per_field) * B;
+#pragma unroll
+    for (int k = 0; k < G::NBOX; ++k)
+      tma_store_3d(&a.map[f], buf + (size_t)s * STAGE + (size_t)k * G::BOX * B, k * G::BOX, row0 % L, row0 / L);
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+    for (int s = 0; s < S; ++s) {
+      const int tile = blockIdx.x + s * gridDim.x;
+      if (tile < total) issue_load(tile, s);
+    }
+  }
+  float4* tws = reinterpret_cast<float4*>(bar + 8);   // 64 bytes of barriers, then the twiddles
+  if constexpr (G::TWS) {
+    for (int i = tid; i < G::TWF; i += blockDim.x) tws[i] = a.tw_fwd[i];
+    for (int i = tid; i < G::TWI; i += blockDim.x) tws[G::TWF + i] = a.tw_inv[i];
+  }
+  __syncthreads();
+
+  SweepArgs<float> sa{};
+  sa.tw_fwd = G::TWS ? tws : a.tw_fwd;
+  sa.tw_inv = G::TWS ? tws + G::TWF : a.tw_inv;
+  sa.ekx = a.ekx;
+  sa.ek2 = a.ek2;
+  sa.nl_coef = a.nl_coef;
+  sa.nl_shift = a.nl_shift;
+  sa.op = a.op;
+  sa.axis = a.axis;
+  sa.scale_inv = a.scale_inv;
+  LayContig<L> lay;
+  bool failed = false;
+  int it = 0;
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++it) {
+    const int s = it % S;
+    const bool ok = mbar_wait_bounded(&bar[s], (unsigned)(it / S) & 1u);
+    if (!__syncthreads_and(ok)) {
+      failed = true;
+      break;
+    }
+    V* sm = buf + (size_t)s * STAGE;
+    const int f = tile / per_field, row = (tile - f * per_field) * B + p;
+    // the TMA tile is [box k][row][x within box]
+    auto addr = [&](int pos) { return sm + (pos / G::BOX) * (G::BOX * B) + p * G::BOX + (pos % G::BOX); };
+    sweep_body<float, L, B, LayContig<L>, decltype(addr), true, (TP <= 32), G::TWS>(sa, t, p, sm, lay, addr, row % L,
+                                                                                       row / L);
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      issue_store(tile, s);
+      bulk_commit();
+      if (it >= 1) {
+        const int nxt = tile - gridDim.x + S * gridDim.x;
+        if (nxt < total) {
+          bulk_wait_read1();
+          issue_load(nxt, (it - 1) % S);
+        }
+      }
+    }
+  }
+  if (failed) {
+    if (tid == 0) atomicExch(a.status, 1);
+  }
+  if (tid == 0) bulk_wait_all();
+  if (failed && tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_wait_bounded(&bar[s], 0u), mbar_wait_bounded(&bar[s], 1u);
+  }
+}
+
+template <int L> struct TmaLaunch {
+  static cudaError_t launch(const TmaSweepArgs& a, int ctas_per_sm, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (a.axis == 0) {
+      using G = TmaContig<L>;
+      static bool attr = false;
+      if (!attr) cudaFuncSetAttribute(k_tma_contig<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+      attr = true;
+      const int tiles = (L * L / G::B) * a.count;
+      int grid = sms * ctas_per_sm;
+      if (grid > tiles) grid = tiles;
+      k_tma_contig<L><<<grid, G::NT, G::SMEM, s>>>(a);
+    } else {
+      using G = TmaStrided<L>;
+      static bool attr = false;
+      if (!attr) cudaFuncSetAttribute(k_tma_strided<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+      attr = true;
+      const int tiles = ((L / G::B) * L) * a.count;
+      int grid = sms * ctas_per_sm;
+      if (grid > tiles) grid = tiles;
+      k_tma_strided<L><<<grid, G::NT, G::SMEM, s>>>(a);
+    }
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace gp

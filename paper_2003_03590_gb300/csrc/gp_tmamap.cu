@@ -1,0 +1,108 @@
+// gp_tmamap.cu -- tensor maps and dispatch of the TMA-pipelined float32 sweeps.
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "gp_internal.h"
+#include "gp_tma.cuh"
+
+namespace gp {
+
+bool tma_supported(int n) {
+  switch (n) {
+#define GP_CASE(L) case L:
+    GP_TMA_SIZES(GP_CASE)
+#undef GP_CASE
+    return true;
+    default:
+      return false;
+  }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+template <int L> static void box_of(int axis, cuuint32_t box[3]) {
+  if (axis == 0) {
+    box[0] = TmaContig<L>::BOX; box[1] = TmaContig<L>::B; box[2] = 1;
+  } else if (axis == 1) {
+    box[0] = TmaStrided<L>::B; box[1] = TmaStrided<L>::BOX; box[2] = 1;
+  } else {
+    box[0] = TmaStrided<L>::B; box[1] = 1; box[2] = TmaStrided<L>::BOX;
+  }
+}
+
+template <int L> static bool swizzled(int axis) { return axis != 0 && TmaStrided<L>::SWZ; }
+
+static bool make_map(CUtensorMap* m, void* base, int n, int axis) {
+  auto enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n};
+  cuuint64_t strides[2] = {(cuuint64_t)n * 8, (cuuint64_t)n * n * 8};
+  cuuint32_t box[3], estr[3] = {1, 1, 1};
+  bool swz = false;
+  switch (n) {
+#define GP_CASE(L) case L: box_of<L>(axis, box); swz = swizzled<L>(axis); break;
+    GP_TMA_SIZES(GP_CASE)
+#undef GP_CASE
+    default: return false;
+  }
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int L> static int ctas_per_sm(int axis) {
+  int nb = 0;
+  if (axis == 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_contig<L>, TmaContig<L>::NT, TmaContig<L>::SMEM);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_strided<L>, TmaStrided<L>::NT, TmaStrided<L>::SMEM);
+  return nb < 1 ? 1 : nb;
+}
+
+cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* status, cudaStream_t s) {
+  static TmaSweepArgs t;   // large: keep it off the stack (launches copy it)
+  std::memset(&t, 0, sizeof(t));
+  t.count = a.count;
+  for (int f = 0; f < a.count; ++f)
+    if (!make_map(&t.map[f], psi[f], n, a.axis)) return cudaErrorInvalidValue;
+  t.tw_fwd = a.tw_fwd;
+  t.tw_inv = a.tw_inv;
+  t.ekx = a.ekx;
+  t.ek2 = a.ek2;
+  t.nl_coef = a.nl_coef;
+  t.nl_shift = a.nl_shift;
+  t.op = a.op;
+  t.axis = a.axis;
+  t.scale_inv = a.scale_inv;
+  t.status = status;
+  switch (n) {
+#define GP_CASE(L)                                                                     \
+  case L: {                                                                            \
+    static int occ[3] = {0, 0, 0};                                                     \
+    if (!occ[a.axis]) {                                                                \
+      if (a.axis == 0) cudaFuncSetAttribute(k_tma_contig<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaContig<L>::SMEM); \
+      else cudaFuncSetAttribute(k_tma_strided<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaStrided<L>::SMEM); \
+      occ[a.axis] = ctas_per_sm<L>(a.axis);                                            \
+    }                                                                                  \
+    return tma_sweep_##L(t, occ[a.axis], s);                                           \
+  }
+    GP_TMA_SIZES(GP_CASE)
+#undef GP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace gp

@@ -63,7 +63,9 @@ def test_autograd_gradient_vs_finite_differences_fp64():
     """dJ/dtheta through the checkpointed adjoint, FP64, vs centred differences (h = 1e-4)."""
     n, dt, m = 16, 0.004, 12
     plan = Plan(field_params(n, dt, xi_over_dx=1.5, precision=GP_FP64))
-    theta0 = torch.from_numpy(OI.srp_theta(n, 0, 3.0)).cuda()
+    # k0 = 2 keeps psi away from zero here (with k0 = 3 a vortex core forms, where the O(h^2) error
+    # of the h = 1e-4 difference reaches 2e-2: the oracle shows the same)
+    theta0 = torch.from_numpy(OI.srp_theta(n, 0, 2.0)).cuda()
     theta = theta0.clone().requires_grad_(True)
     psiT = GPEvolve.apply(theta, plan, m, 4)
     J = IncompressibleKineticEnergy.apply(psiT, plan, 1e-6)
@@ -80,7 +82,7 @@ def test_autograd_gradient_vs_finite_differences_fp64():
     for seed in range(3):
         v = torch.from_numpy(np.real(random_direction(n, 50 + seed, complex_valued=False))).cuda()
         an = float((g * v).sum())
-        for h, tol in ((1e-4, 1e-3), (1e-5, 1e-5)):
+        for h, tol in ((1e-4, 1e-3), (1e-5, 1e-6)):
             fd = (Jof(theta0 + h * v) - Jof(theta0 - h * v)) / (2 * h)
             assert abs(fd - an) < tol * abs(fd), (seed, h, fd, an)
     # and against the oracle's adjoint gradient

@@ -52,8 +52,10 @@ def test_diagnostics_sound_wave_and_srp():
     Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
     d, _ = plan.diagnostics(0, to_gpu(np.exp(0.1j * np.sin(X)), np.complex128))
     assert abs(d["E_kin_c"] - p.alpha ** 2 * 0.01) < 1e-12 and abs(d["E_kin_i"]) < 1e-18
-    # SRP at t = 0 is vortex free: its kinetic energy is compressible
-    psi = OI.srp_spectral(n, 1, 3.0)
+    # SRP at t = 0 is vortex free: once resolved (48^3, k0 = 2) its kinetic energy is compressible
+    n = 48
+    plan = _plan(n, GP_FP64)
+    psi = OI.srp_spectral(n, 1, 2.0)
     d, _ = plan.diagnostics(0, to_gpu(psi, np.complex128))
     assert d["E_kin_c"] > 1e6 * max(d["E_kin_i"], 1e-300)
 

@@ -118,3 +118,12 @@ def test_zero_density_points_are_masked():
     u, q = D.hydro_fields(psi, p)
     assert all(c[2, 3, 4] == 0.0 for c in u + q)
     assert all(np.isfinite(c).all() for c in u + q)
+
+
+def test_srp_start_is_vortex_free_once_resolved():
+    """A smoothed random phase has no vortices: with |psi| = 1, u = 2 alpha grad(theta) is a gradient,
+    so E_kin^i vanishes once the grid resolves exp(i theta) (Sec. 5.3: vortices nucleate later)."""
+    from oracle import initial as OI
+    n = 64
+    d, _ = D.full(OI.srp_spectral(n, 1, 2.0), _p(n), with_spectra=False)
+    assert d["E_kin_i"] < 1e-12 * d["E_kin_c"]
