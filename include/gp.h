@@ -156,6 +156,27 @@ gp_status gp_ekin_i_grad(gp_plan* plan, int field, const void* psi, void* lambda
  * (float for GP_FP32, double for GP_FP64). */
 gp_status gp_phase_grad(gp_plan* plan, int field, const void* psi, const void* lambda, void* grad_theta);
 
+/* Diagnostics of a float32 (complex64) field of N^3 points, N in {8, 12, 16, 24, 32, 48, 64},
+ * that allocate no device memory and need no plan -- for callers that cannot call cudaMalloc:
+ * code embedded in an application whose caching allocator already holds the device's memory,
+ * or a monitoring hook inside a latency-critical loop where an allocation would stall every
+ * stream of the device.  (The paper has no counterpart; it is the same computation as
+ * gp_diagnostics, with the same outputs and the same readings.)
+ *   alpha, beta: the field's coefficients;  psi: device field, 16-byte aligned;
+ *   out, spectra (NULL or 4*nbins doubles), nbins: as for gp_diagnostics;
+ *   cuda_stream: cudaStream_t or NULL for the legacy default stream; synchronised on return.
+ * Scratch: file-scope device arrays of fixed size inside the library -- four 64^3 complex64
+ * work fields (8 MiB), twiddle tables, accumulators and a histogram, about 8.4 MiB in all --
+ * which every GPU that loads the library keeps until the process exits.  N > 64 (or any other
+ * unsupported N) returns GP_ERR_UNSUPPORTED_SIZE without touching the device.
+ * The first call on a device resolves the arrays' device addresses and uploads the twiddle
+ * tables (cudaGetSymbolAddress, cudaMemcpy); make that first call before any stream capture.
+ * All calls share the arrays, which keep the last call's contents (each call clears the
+ * accumulators it uses): calls that overlap on the GPU -- from two streams or two host
+ * threads -- race on them and must be serialised by the caller. */
+gp_status gp_diagnostics_noalloc(int n, double alpha, double beta, const void* psi, gp_diag* out, double* spectra,
+                                 int nbins, void* cuda_stream);
+
 /* Instrumentation (no counterpart in the paper).
  * gp_profile(plan, 1) clears the records and makes later gp_step calls launch every
  * float32 sweep directly (no graph replay) between a pair of CUDA events on the plan's

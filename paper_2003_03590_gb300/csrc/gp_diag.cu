@@ -250,3 +250,168 @@ extern "C" gp_status gp_diagnostics(gp_plan* p, int field, const void* psi, gp_d
   if (p->f[field].fp64) return diag_impl<double>(p, field, (const cpx<double>*)psi, out, spectra, nbins);
   return diag_impl<float>(p, field, (const cpx<float>*)psi, out, spectra, nbins);
 }
+
+// ---------------------------------------------------------------- allocation-free diagnostics
+// gp_diagnostics_noalloc: the diagnostics above for float32 fields of at most 64^3 points,
+// for callers that must not allocate device memory -- for example code running inside an
+// application whose caching allocator already owns all device memory (a cudaMalloc would fail
+// or fragment it), or a monitoring hook in a latency-critical loop where cudaMalloc would
+// stall every stream of the device while it synchronises.  It needs no plan: every buffer
+// it uses is a file-scope __device__ array below, reserved when the library is loaded and
+// kept by every GPU that loads it until the process exits:
+//   4 work fields of 64^3 complex64 (8 MiB), the float32 twiddle tables of the supported
+//   lengths up to 64, reduction accumulators, a status word and the shell histogram.
+// All calls share these arrays, which keep the last call's contents; every call clears the
+// accumulators and histogram it uses.  Calls that overlap on the GPU (two streams, two host
+// threads) race on them: serialise them.
+
+namespace gp {
+
+constexpr int NOALLOC_MAX_N = 64;
+constexpr long long NOALLOC_MAX_PTS = (long long)NOALLOC_MAX_N * NOALLOC_MAX_N * NOALLOC_MAX_N;
+constexpr int NOALLOC_MAX_BINS = 64;     // >= floor(sqrt(3) 64 / 2 + 1/2) + 1 = 56
+constexpr int NOALLOC_TW = 1024;         // float4 twiddle entries for all lengths <= 64, both directions
+constexpr int NOALLOC_SIZES[7] = {8, 12, 16, 24, 32, 48, 64};
+
+static __device__ __align__(256) float2 g_na_work[4 * NOALLOC_MAX_PTS];
+static __device__ __align__(256) float4 g_na_tw[NOALLOC_TW];
+static __device__ __align__(256) double g_na_acc[8];
+static __device__ __align__(256) double g_na_spec[4 * NOALLOC_MAX_BINS];
+static __device__ __align__(256) int g_na_flag[4];
+
+// host-side record of what set-up resolved on each device (indexed by device ordinal)
+struct NoAllocDevice {
+  bool ready = false;
+  float2* work = nullptr;
+  float4* tw = nullptr;
+  double* acc = nullptr;
+  double* spec = nullptr;
+  int* flag = nullptr;
+  int tw_off[7][2] = {};   // offset of each length's (forward, inverse) table in tw
+};
+static NoAllocDevice g_na_dev[64];
+
+// Stockham twiddles (same definition as the plan's tables) written into a fixed host array.
+static int noalloc_twiddles(int n, bool inv, float4* out, int cap) {
+  const int np = plan_np(n);
+  int ns = 1, k = 0;
+  for (int i = 0; i < np; ++i) {
+    const int R = plan_radix_fwd(n, inv ? np - 1 - i : i);
+    for (int jm = 0; jm < ns; ++jm)
+      for (int r = 1; r < R; ++r) {
+        if (k >= cap) return -1;
+        const long long den = (long long)ns * R, num = ((long long)r * jm) % den;
+        const double ang = (inv ? 2.0 : -2.0) * M_PI * (double)num / (double)den;
+        float ch, cl, sh, sl;
+        split_hilo(std::cos(ang), &ch, &cl);
+        split_hilo(std::sin(ang), &sh, &sl);
+        out[k++] = make_float4(ch, sh, cl, sl);
+      }
+    ns *= R;
+  }
+  return k;
+}
+
+// Once per device, with that device current: resolve the device addresses of the arrays
+// (their names in host code only stand in for them) and upload the twiddle tables.
+static gp_status noalloc_setup(int dev, NoAllocDevice& D) {
+  if (cudaGetSymbolAddress((void**)&D.work, g_na_work) != cudaSuccess) return GP_ERR_CUDA;
+  if (cudaGetSymbolAddress((void**)&D.tw, g_na_tw) != cudaSuccess) return GP_ERR_CUDA;
+  if (cudaGetSymbolAddress((void**)&D.acc, g_na_acc) != cudaSuccess) return GP_ERR_CUDA;
+  if (cudaGetSymbolAddress((void**)&D.spec, g_na_spec) != cudaSuccess) return GP_ERR_CUDA;
+  if (cudaGetSymbolAddress((void**)&D.flag, g_na_flag) != cudaSuccess) return GP_ERR_CUDA;
+  float4 host[NOALLOC_TW];
+  int used = 0;
+  for (int q = 0; q < 7; ++q)
+    for (int inv = 0; inv < 2; ++inv) {
+      const int k = noalloc_twiddles(NOALLOC_SIZES[q], inv != 0, host + used, NOALLOC_TW - used);
+      if (k < 0) return GP_ERR_CUDA;
+      D.tw_off[q][inv] = used;
+      used += k > 0 ? k : 1;   // keep distinct offsets even for single-pass lengths
+    }
+  if (cudaMemcpy(D.tw, host, sizeof(float4) * used, cudaMemcpyHostToDevice) != cudaSuccess) return GP_ERR_CUDA;
+  (void)dev;
+  D.ready = true;
+  return GP_OK;
+}
+
+}  // namespace gp
+
+extern "C" gp_status gp_diagnostics_noalloc(int n, double alpha, double beta, const void* psi, gp_diag* out,
+                                            double* spectra, int nbins, void* cuda_stream) {
+  using namespace gp;
+  int q = -1;
+  for (int i = 0; i < 7; ++i)
+    if (NOALLOC_SIZES[i] == n) q = i;
+  if (q < 0) return GP_ERR_UNSUPPORTED_SIZE;   // n > 64 or not a supported length
+  if (!psi || ((uintptr_t)psi & 15) || !out || !std::isfinite(alpha) || !std::isfinite(beta))
+    return GP_ERR_INVALID_ARG;
+  const int nb = (int)std::floor(std::sqrt(3.0) * n / 2.0 + 0.5) + 1;
+  if (spectra && nbins < nb) return GP_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ERR_CUDA;
+  NoAllocDevice& D = g_na_dev[dev];
+  if (!D.ready) {
+    gp_status st = noalloc_setup(dev, D);
+    if (st != GP_OK) return st;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const long long npts = (long long)n * n * n;
+  // a stack view of a plan field that points at the static tables (no allocation)
+  FieldPlan F;
+  F.n = n;
+  F.npts = npts;
+  F.alpha = alpha;
+  F.beta = beta;
+  F.t32.tw_fwd = D.tw + D.tw_off[q][0];
+  F.t32.tw_inv = D.tw + D.tw_off[q][1];
+  const cpx<float>* x = (const cpx<float>*)psi;
+  cpx<float>* w0 = D.work;
+  cpx<float>* w1 = w0 + npts;
+  cpx<float>* w2 = w1 + npts;
+  cpx<float>* w3 = w2 + npts;
+  const unsigned g = rgrid(npts);
+  if (cudaMemsetAsync(D.acc, 0, 8 * sizeof(double), s) != cudaSuccess) return GP_ERR_CUDA;
+  if (cudaMemsetAsync(D.flag, 0, sizeof(int), s) != cudaSuccess) return GP_ERR_CUDA;
+  if (cudaMemsetAsync(D.spec, 0, (size_t)4 * nb * sizeof(double), s) != cudaSuccess) return GP_ERR_CUDA;
+  k_phys1<float><<<g, 256, 0, s>>>(x, npts, D.acc, D.flag);
+  if (cudaMemcpyAsync(w0, x, (size_t)npts * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GP_ERR_CUDA;
+  if (fft3<float>(F, w0, false, s) != cudaSuccess) return GP_ERR_CUDA;
+  k_kspace1<float><<<g, 256, 0, s>>>(w0, w1, w2, w3, n, D.acc + 2);
+  if (fft3<float>(F, w1, true, s) != cudaSuccess || fft3<float>(F, w2, true, s) != cudaSuccess ||
+      fft3<float>(F, w3, true, s) != cudaSuccess)
+    return GP_ERR_CUDA;
+  k_phys2<float><<<g, 256, 0, s>>>(x, w0, w1, w2, w3, npts, alpha, D.acc + 3);
+  for (cpx<float>* w : {w0, w1, w2, w3})
+    if (fft3<float>(F, w, false, s) != cudaSuccess) return GP_ERR_CUDA;
+  k_kspace2<float><<<g, 256, (size_t)4 * nb * sizeof(double), s>>>(w0, w1, w2, w3, n, nb, alpha, beta, D.spec);
+  if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
+  double acc[8];
+  double hs[4 * NOALLOC_MAX_BINS];
+  int flag = 0;
+  if (cudaMemcpyAsync(acc, D.acc, sizeof(acc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(&flag, D.flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(hs, D.spec, (size_t)4 * nb * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return GP_ERR_CUDA;
+  if (flag) return GP_ERR_NONFINITE;
+  const double dn = (double)npts, dn2 = dn * dn;
+  gp_diag d{};
+  d.N = acc[0] / dn;
+  d.E_int = alpha * beta * acc[1] / dn;
+  d.E = 2.0 * alpha * alpha * acc[2] / dn2 + d.E_int;
+  d.E_kin = acc[3] / dn;
+  d.E_q = acc[4] / dn;
+  double si = 0.0, sc = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    si += hs[b];
+    sc += hs[nb + b];
+  }
+  d.E_kin_i = si / dn2;
+  d.E_kin_c = sc / dn2;
+  *out = d;
+  if (spectra)
+    for (int c = 0; c < 4; ++c)
+      for (int b = 0; b < nb; ++b) spectra[c * nbins + b] = hs[(size_t)c * nb + b] / dn2;
+  return GP_OK;
+}
