@@ -61,7 +61,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gp_fft.cuh", "gp_sweep.cuh"):
+    for f in ("gp_fft.cuh", "gp_sweep.cuh", "gp_tma.cuh"):
         with open(os.path.join(ROOT, "paper_2003_03590_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -168,6 +168,13 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def tuned_choices(plan, n):
+    names = {0: "tma", 1: "tma_1cta", 2: "plain"}
+    kinds = {"z:n_fwd": (2, 4), "z:inv_n_fwd": (2, 3), "z:inv_n": (2, 5), "y:fwd": (1, 1), "y:inv": (1, 2),
+             "x:fwd_k_inv": (0, 6)}
+    return {k: names.get(plan.sweep_variant(n, a, o), "?") for k, (a, o) in kinds.items()}
+
+
 def make_plan(gq, n, dt, prec):
     return gq.Plan(gq.field_params(n, dt, xi_over_dx=1.5, precision=prec))
 
@@ -216,16 +223,18 @@ def roofline_of(gq, plan, psi, n, ksteps, peak):
 
 def ensemble_leg(gq, steps=500):
     """24 x 64^3 + 16 x 96^3 + 8 x 128^3 smoothed-random-phase fields (seeds 0..47, k0 = 4),
-    dt = 0.004, advanced together by one plan (one launch per sweep and size class, the
-    four-sweep cycle replayed from a CUDA graph) against the same fields advanced one plan
-    at a time."""
+    dt = 0.004, advanced together by one plan (one launch per sweep and size class; the timed
+    call repeats an untimed call of the same length, so the whole 500-step run replays as one
+    captured CUDA graph) against the same fields advanced one plan at a time."""
     import torch
     sizes = [64] * 24 + [96] * 16 + [128] * 8
     fields = [gq.field_params(n, 0.004, xi_over_dx=1.5) for n in sizes]
-    batch = gq.Plan(fields)
+    import tempfile
+    cache = os.path.join(tempfile.mkdtemp(), "tune.json")
+    batch = gq.Plan(fields).autotune(cache)
     psis = [batch.init_srp(i, batch.empty(i), seed=i, mode=0, p0=4.0, p1=math.pi) for i in range(len(sizes))]
     pts = sum(n ** 3 for n in sizes)
-    batch.step(psis, 5)
+    batch.step(psis, steps)                     # untimed: the next call of this length is one graph
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = gq.launch_count(batch)
@@ -235,9 +244,9 @@ def ensemble_leg(gq, steps=500):
     torch.cuda.synchronize()
     ms_b = e0.elapsed_time(e1)
     launches = gq.launch_count(batch) - l0
-    singles = [gq.Plan(f) for f in fields]
+    singles = [gq.Plan(f).autotune(cache) for f in fields]     # the same kernel choices
     for pl, f in zip(singles, psis):
-        pl.step([f], 5)
+        pl.step([f], steps)
     torch.cuda.synchronize()
     e0.record(singles[0].stream)
     for pl, f in zip(singles, psis):
@@ -246,7 +255,7 @@ def ensemble_leg(gq, steps=500):
     torch.cuda.synchronize()
     ms_s = e0.elapsed_time(e1)
     return {"points": pts, "steps": steps, "batched": {"value": pts * steps / (ms_b / 1e3), "ms": ms_b,
-                                                       "launches": launches},
+                                                       "launches": launches, "graph_launches": 1},
             "sequential": {"value": pts * steps / (ms_s / 1e3), "ms": ms_s}, "speedup": ms_s / ms_b}
 
 
@@ -267,10 +276,18 @@ def adjoint_leg(gq, n=128, steps=400, every=20):
         J = gq.IncompressibleKineticEnergy.apply(gq.GPEvolve.apply(t, plan, steps, every), plan, 1e-6)
         J.backward()
         torch.cuda.synchronize()
-        out[name] = {"seconds": time.perf_counter() - t0, "J": float(J)}
+        out[name] = {"seconds": time.perf_counter() - t0, "J": float(J.detach())}
         grads[name] = t.grad.double()
+    # sensitivity of the float64 gradient itself to the float32 rounding of the start
+    plan = gq.Plan(gq.field_params(n, 0.004, xi_over_dx=1.5, precision=gq.GP_FP64))
+    t = th.to(torch.float32).to(torch.float64).cuda().requires_grad_(True)
+    J = gq.IncompressibleKineticEnergy.apply(gq.GPEvolve.apply(t, plan, steps, every), plan, 1e-6)
+    J.backward()
+    g64r = t.grad.double()
     g32, g64 = grads["fp32"], grads["fp64"]
-    out["grad_rel_err_fp32_vs_fp64"] = float(torch.linalg.vector_norm(g32 - g64) / torch.linalg.vector_norm(g64))
+    rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    out["grad_rel_err_fp32_vs_fp64"] = rel(g32, g64)
+    out["grad_rel_err_fp64_rounded_start_vs_fp64"] = rel(g64r, g64)
     return out
 
 
@@ -333,6 +350,7 @@ def main():
     n, K, W = N_MAIN, args.steps, max(3, args.warmup)
 
     plan = make_plan(gq, n, DT_MAIN, gq.GP_FP32)
+    plan.autotune()                            # kernel choice per sweep kind, before any timing
     psi = init_rvr(gq, plan, seed=rank)
     plan.step([psi], W)                       # warm-up (also captures the step graph)
     torch.cuda.synchronize()
@@ -383,7 +401,8 @@ def main():
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"GP split step {n}^3, xi=1.5dx, dt={DT_MAIN}, RVR {RINGS} rings, fused FP32",
                        "global_batch": world, "seq_len": n ** 3, "parallelism": f"replicas x{world}",
-                       "l2": f"field {8 * n ** 3 / 1e6:.0f} MB > 129 MB L2; no flush between steps"},
+                       "l2": f"field {8 * n ** 3 / 1e6:.0f} MB > 129 MB L2; no flush between steps",
+                       "tuned": tuned_choices(plan, n)},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
 
     if not args.no_extras and rank == 0:
@@ -426,7 +445,7 @@ def main():
         # larger grids
         sizes = {}
         for s in [int(v) for v in args.sizes.split(",") if v.strip()]:
-            ps = make_plan(gq, s, 0.001, gq.GP_FP32)
+            ps = make_plan(gq, s, 0.001, gq.GP_FP32).autotune()
             f = ps.init_srp(0, ps.empty(), seed=0, mode=0, p0=8.0, p1=math.pi)
             ps.step([f], 5)
             ks = 100 if s <= 512 else 40

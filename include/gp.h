@@ -190,6 +190,17 @@ int gp_profile_read(gp_plan* plan, int max_kinds, char* names, long long* launch
 /* Number of kernels this plan has launched (or replayed inside graphs) since creation. */
 long long gp_launch_count(const gp_plan* plan);
 
+/* Autotuner of the float32 sweep kernels (no counterpart in the paper).  For every grid length
+ * of the plan's float32 fields and every sweep of its time step (z: inverse/N/forward variants,
+ * y: forward and inverse, x: forward, K, inverse) it times the candidate kernels on a scratch
+ * field (allocated and freed here) and keeps the fastest: 0 the TMA-pipelined persistent kernel
+ * at full occupancy, 1 the same with one CTA per SM, 2 the non-persistent kernel.  cache_path
+ * (NULL: none) names a JSON file of earlier choices keyed by GPU name, length, axis and operation;
+ * cached choices are reused without timing and new ones are added.  Synchronises the stream and
+ * drops captured graphs.  gp_plan_sweep_variant returns the variant in use for a sweep kind. */
+gp_status gp_plan_autotune(gp_plan* plan, const char* cache_path);
+int gp_plan_sweep_variant(gp_plan* plan, int n, int axis, int op);
+
 /* Message of the last failed call on this plan ("" if none); valid until the next call. */
 const char* gp_last_error(const gp_plan* plan);
 

@@ -117,6 +117,32 @@ __global__ void k_phys2(const cpx<T>* __restrict__ psi, cpx<T>* w0, cpx<T>* w1, 
   block_add<2>(v, acc);
 }
 
+// Add v[0..4) to hist[q * nbins + b] for every lane of a warp (b < 0: nothing).  Runs of equal b
+// over consecutive lanes (consecutive kx in a row: the shell changes slowly) are summed with a
+// segmented shuffle scan first, so one atomic per run reaches shared memory instead of one per lane.
+__device__ __forceinline__ void bin_add(double* hist, int nbins, int b, double (&v)[4]) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int bprev = __shfl_up_sync(full, b, 1);
+  const unsigned heads = __ballot_sync(full, lane == 0 || bprev != b);
+  const int start = 31 - __clz(heads & ((2u << lane) - 1u));   // first lane of this lane's run
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] = __shfl_up_sync(full, v[q], o);
+    if (lane - o >= start) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] += t[q];
+    }
+  }
+  const int bnext = __shfl_down_sync(full, b, 1);
+  if ((lane == 31 || bnext != b) && b >= 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) atomicAdd(&hist[q * nbins + b], v[q]);
+  }
+}
+
 // Helmholtz split and shell binning; spec layout [4][nbins]: E_kin^i, E_kin^c, E_q, E_int (unscaled)
 template <typename T>
 __global__ void k_kspace2(const cpx<T>* __restrict__ w0, const cpx<T>* __restrict__ w1, const cpx<T>* __restrict__ w2,
@@ -126,43 +152,56 @@ __global__ void k_kspace2(const cpx<T>* __restrict__ w0, const cpx<T>* __restric
   __syncthreads();
   const long long npts = (long long)n * n * n;
   const cpx<T>* ws[3] = {w1, w2, w3};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
-    const int mx = (n - ix) % n, my = (n - iy) % n, mz = (n - iz) % n;
-    const long long im = ((long long)mz * n + my) * n + mx;
-    const double kx = wavenumber(ix, n), ky = wavenumber(iy, n), kz = wavenumber(iz, n);
-    int b = (int)floor(sqrt(kx * kx + ky * ky + kz * kz) + 0.5);
-    if (b >= nbins) b = nbins - 1;
-    const double kd[3] = {(double)wavenumber_d(ix, n), (double)wavenumber_d(iy, n), (double)wavenumber_d(iz, n)};
-    double ur[3], ui[3], eq = 0.0;
+  const int lane = threadIdx.x & 31;
+  // warp-uniform trip count: lane i of a warp handles base + i
+  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < npts;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + lane;
+    int b = -1;
+    double val[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < npts) {
+      // per-point arithmetic in the field's precision (float64 is slow on this part); the sums that
+      // follow are float64
+      using S = T;
+      const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
+      const int mx = (n - ix) % n, my = (n - iy) % n, mz = (n - iz) % n;
+      const long long im = ((long long)mz * n + my) * n + mx;
+      const int kx = wavenumber(ix, n), ky = wavenumber(iy, n), kz = wavenumber(iz, n);
+      b = (int)floor(sqrt((double)(kx * kx + ky * ky + kz * kz)) + 0.5);
+      if (b >= nbins) b = nbins - 1;
+      const S kd[3] = {(S)wavenumber_d(ix, n), (S)wavenumber_d(iy, n), (S)wavenumber_d(iz, n)};
+      S ur[3], ui[3], eq = 0;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      cpx<T> z = ws[j][i], zm = ws[j][im];
-      // u_k = (Z(k) + conj(Z(-k))) / 2,  q_k = (Z(k) - conj(Z(-k))) / (2 i)
-      ur[j] = 0.5 * ((double)z.x + zm.x);
-      ui[j] = 0.5 * ((double)z.y - zm.y);
-      const double qr = 0.5 * ((double)z.y + zm.y), qi = -0.5 * ((double)z.x - zm.x);
-      eq += qr * qr + qi * qi;
-    }
-    const double kk = kd[0] * kd[0] + kd[1] * kd[1] + kd[2] * kd[2];
-    double cr = 0.0, ci = 0.0;
-    if (kk > 0.0) {
-      cr = (kd[0] * ur[0] + kd[1] * ur[1] + kd[2] * ur[2]) / kk;
-      ci = (kd[0] * ui[0] + kd[1] * ui[1] + kd[2] * ui[2]) / kk;
-    }
-    double ei = 0.0, ec = 0.0;
+      for (int j = 0; j < 3; ++j) {
+        cpx<T> z = ws[j][i], zm = ws[j][im];
+        // u_k = (Z(k) + conj(Z(-k))) / 2,  q_k = (Z(k) - conj(Z(-k))) / (2 i)
+        ur[j] = S(0.5) * (z.x + zm.x);
+        ui[j] = S(0.5) * (z.y - zm.y);
+        const S qr = S(0.5) * (z.y + zm.y), qi = S(-0.5) * (z.x - zm.x);
+        eq += qr * qr + qi * qi;
+      }
+      const S kk = kd[0] * kd[0] + kd[1] * kd[1] + kd[2] * kd[2];
+      S cr = 0, ci = 0;
+      if (kk > S(0)) {
+        const S inv = S(1) / kk;
+        cr = (kd[0] * ur[0] + kd[1] * ur[1] + kd[2] * ur[2]) * inv;
+        ci = (kd[0] * ui[0] + kd[1] * ui[1] + kd[2] * ui[2]) * inv;
+      }
+      S ei = 0, ec = 0;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const double ucr = kd[j] * cr, uci = kd[j] * ci;
-      ec += ucr * ucr + uci * uci;
-      const double uir = ur[j] - ucr, uii = ui[j] - uci;
-      ei += uir * uir + uii * uii;
+      for (int j = 0; j < 3; ++j) {
+        const S ucr = kd[j] * cr, uci = kd[j] * ci;
+        ec += ucr * ucr + uci * uci;
+        const S uir = ur[j] - ucr, uii = ui[j] - uci;
+        ei += uir * uir + uii * uii;
+      }
+      cpx<T> r = w0[i];
+      val[0] = 0.5 * (double)ei;
+      val[1] = 0.5 * (double)ec;
+      val[2] = 2.0 * alpha * alpha * (double)eq;
+      val[3] = alpha * beta * ((double)r.x * r.x + (double)r.y * r.y);
     }
-    cpx<T> r = w0[i];
-    atomicAdd(&hist[b], 0.5 * ei);
-    atomicAdd(&hist[nbins + b], 0.5 * ec);
-    atomicAdd(&hist[2 * nbins + b], 2.0 * alpha * alpha * eq);
-    atomicAdd(&hist[3 * nbins + b], alpha * beta * ((double)r.x * r.x + (double)r.y * r.y));
+    bin_add(hist, nbins, b, val);
   }
   __syncthreads();
   for (int b = threadIdx.x; b < 4 * nbins; b += blockDim.x)

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "gp.h"
@@ -23,7 +24,8 @@ GP_TMA_SIZES(GP_DECL_TMA)
 #undef GP_DECL_TMA
 bool tma_supported(int n);
 // launch one TMA sweep for the fields psi[0..count) of length n (float32 fused path)
-cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* status, cudaStream_t s);
+cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* status, cudaStream_t s,
+                      int ctas_req = 0);   // CTAs per SM; 0: as many as fit
 
 bool supported_n(int n);
 void split_hilo(double v, float* hi, float* lo);   // see gp_plan.cu
@@ -70,8 +72,12 @@ struct gp_plan {
   cudaGraphExec_t cycle_graph = nullptr;   // captured steady-state cycle of gp_step
   std::vector<void*> cycle_key;            // field pointers the graph was captured for
   int cycle_len = 0;
+  cudaGraphExec_t run_graph = nullptr;     // a whole gp_step call, captured when it repeats
+  std::vector<void*> run_key, last_key;
+  int run_steps = -1, last_steps = -1;
   long long launches = 0;                  // kernels launched or replayed
   bool use_tma = true;                     // float32 sweeps through the TMA-pipelined kernels
+  std::vector<std::pair<long long, int>> tune;   // (n, axis, op) key -> sweep variant (gp_plan_autotune)
   bool prof = false;                       // per-launch event timing (gp_profile)
   std::vector<cudaEvent_t> ev_pool;        // recorded events, two per profiled launch
   std::vector<int> ev_kind;                // kind index of each profiled launch

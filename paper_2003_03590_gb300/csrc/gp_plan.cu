@@ -344,6 +344,7 @@ gp_status gp_plan_destroy(gp_plan* p) {
   if (p->flag) cudaFree(p->flag);
   if (p->adj_ws) cudaFree(p->adj_ws);
   if (p->cycle_graph) cudaGraphExecDestroy(p->cycle_graph);
+  if (p->run_graph) cudaGraphExecDestroy(p->run_graph);
   delete p;
   return GP_OK;
 }

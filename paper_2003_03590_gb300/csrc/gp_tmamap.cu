@@ -62,7 +62,7 @@ static bool make_map(CUtensorMap* m, void* base, int n, int axis) {
   return r == CUDA_SUCCESS;
 }
 
-template <int L> static int ctas_per_sm(int axis) {
+template <int L> static int occupancy_ctas(int axis) {
   int nb = 0;
   if (axis == 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_contig<L>, TmaContig<L>::NT, TmaContig<L>::SMEM);
@@ -71,7 +71,8 @@ template <int L> static int ctas_per_sm(int axis) {
   return nb < 1 ? 1 : nb;
 }
 
-cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* status, cudaStream_t s) {
+cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* status, cudaStream_t s,
+                      int ctas_req) {
   static TmaSweepArgs t;   // large: keep it off the stack (launches copy it)
   std::memset(&t, 0, sizeof(t));
   t.count = a.count;
@@ -94,9 +95,10 @@ cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* s
     if (!occ[a.axis]) {                                                                \
       if (a.axis == 0) cudaFuncSetAttribute(k_tma_contig<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaContig<L>::SMEM); \
       else cudaFuncSetAttribute(k_tma_strided<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaStrided<L>::SMEM); \
-      occ[a.axis] = ctas_per_sm<L>(a.axis);                                            \
+      occ[a.axis] = occupancy_ctas<L>(a.axis);                                            \
     }                                                                                  \
-    return tma_sweep_##L(t, occ[a.axis], s);                                           \
+    if (occ[a.axis] < 1) return cudaErrorInvalidConfiguration;                                   \
+    return tma_sweep_##L(t, ctas_req > 0 && ctas_req < occ[a.axis] ? ctas_req : occ[a.axis], s); \
   }
     GP_TMA_SIZES(GP_CASE)
 #undef GP_CASE

@@ -163,6 +163,15 @@ class Plan:
                                              _ptr(self._field(lam, field)), float(eps), ctypes.byref(J)))
         return lam, J.value
 
+    def autotune(self, cache_path=None):
+        """Pick the fastest float32 sweep kernel per grid length and sweep kind (see gp.h)."""
+        path = None if cache_path is None else str(cache_path).encode()
+        self._check(self._lib.gp_plan_autotune(self._h, path))
+        return self
+
+    def sweep_variant(self, n, axis, op):
+        return self._lib.gp_plan_sweep_variant(self._h, n, axis, op)
+
     def phase_grad(self, field, psi, lam):
         n = self.n(field)
         g = torch.empty((n, n, n), dtype=self.real_dtype(field), device="cuda")

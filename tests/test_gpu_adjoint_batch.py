@@ -137,3 +137,48 @@ def test_mixed_precision_batch():
     b = to_gpu(psi0, np.complex64)
     plan.step([a, b], 5)
     assert rel_l2(to_np(b), to_np(a)) < 5e-6
+
+
+def test_repeated_call_replays_whole_run_graph_bitwise():
+    """A gp_step call repeated with the same fields and step count replays one captured graph of
+    the whole run; its result is bitwise the result of the launches it replaces."""
+    dt = 0.004
+    sizes = [16, 16, 24]
+    a = Plan([field_params(n, dt, xi_over_dx=1.5) for n in sizes])
+    b = Plan([field_params(n, dt, xi_over_dx=1.5) for n in sizes])
+    fa = [to_gpu(random_psi(n, 40 + i), np.complex64) for i, n in enumerate(sizes)]
+    fb = [f.clone() for f in fa]
+    from paper_2003_03590_gb300.gpqt import launch_count
+    for _ in range(3):                      # calls 2 and 3 of plan a replay the whole-run graph
+        l0 = launch_count(a)
+        a.step(fa, 7)
+        assert launch_count(a) - l0 == 2 * (4 * 7 + 1)   # two groups (16^3 x2, 24^3), 4 sweeps per step + 1
+    other = [f.clone() for f in fa]
+    for _ in range(3):                      # alternating field sets: never the whole-run graph
+        b.step(fb, 7)
+        b.step(other, 7)
+    torch.cuda.synchronize()
+    for x, y in zip(fa, fb):
+        assert torch.equal(x, y)
+
+
+def test_autotune_picks_variants_and_caches(tmp_path):
+    dt = 0.004
+    sizes = [32, 48]
+    cache = tmp_path / "tune.json"
+    tuned = Plan([field_params(n, dt, xi_over_dx=1.5) for n in sizes]).autotune(cache)
+    text = cache.read_text()
+    assert text.count("|") >= 2 * 8 * 3          # 8 sweep kinds per length, 3 separators per key
+    for n in sizes:
+        for axis, op in ((2, 3), (1, 1), (1, 2), (0, 6)):
+            assert tuned.sweep_variant(n, axis, op) in (0, 1, 2)
+    again = Plan([field_params(n, dt, xi_over_dx=1.5) for n in sizes]).autotune(cache)   # from the cache
+    for n in sizes:
+        assert again.sweep_variant(n, 0, 6) == tuned.sweep_variant(n, 0, 6)
+    plain = Plan([field_params(n, dt, xi_over_dx=1.5) for n in sizes])
+    fa = [to_gpu(random_psi(n, 60 + i), np.complex64) for i, n in enumerate(sizes)]
+    fb = [f.clone() for f in fa]
+    tuned.step(fa, 6)
+    plain.step(fb, 6)
+    for x, y in zip(fa, fb):
+        assert rel_l2(to_np(x), to_np(y)) < 1e-6
