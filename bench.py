@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip fp64/cufft/large-size/cpu legs")
     ap.add_argument("--sizes", default="512,1024")
     ap.add_argument("--only-step", action="store_true", help="init, warm-up and the timed steps only (profiling)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of kernel choices: read if present (no tuning launches), else written")
     return ap.parse_args()
 
 
@@ -61,7 +63,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("gp_fft.cuh", "gp_sweep.cuh", "gp_tma.cuh"):
+    for f in ("gp_fft.cuh", "gp_sweep.cuh", "gp_tma.cuh", "gp_plane.cuh"):
         with open(os.path.join(ROOT, "paper_2003_03590_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -169,10 +171,12 @@ def max_over_ranks(x, world):
 
 
 def tuned_choices(plan, n):
-    names = {0: "tma", 1: "tma_1cta", 2: "plain"}
+    names = {0: "tma", 1: "tma_1cta", 2: "plain", 3: "tma_2stage"}
     kinds = {"z:n_fwd": (2, 4), "z:inv_n_fwd": (2, 3), "z:inv_n": (2, 5), "y:fwd": (1, 1), "y:inv": (1, 2),
              "x:fwd_k_inv": (0, 6)}
-    return {k: names.get(plan.sweep_variant(n, a, o), "?") for k, (a, o) in kinds.items()}
+    out = {k: names.get(plan.sweep_variant(n, a, o), "?") for k, (a, o) in kinds.items()}
+    out["y_x_y"] = "fused plane kernel" if plan.sweep_variant(n, 1, 7) == 0 else "three sweeps"
+    return out
 
 
 def make_plan(gq, n, dt, prec):
@@ -350,7 +354,7 @@ def main():
     n, K, W = N_MAIN, args.steps, max(3, args.warmup)
 
     plan = make_plan(gq, n, DT_MAIN, gq.GP_FP32)
-    plan.autotune()                            # kernel choice per sweep kind, before any timing
+    plan.autotune(args.tune_cache)             # kernel choice per sweep kind, before any timing
     psi = init_rvr(gq, plan, seed=rank)
     plan.step([psi], W)                       # warm-up (also captures the step graph)
     torch.cuda.synchronize()
@@ -375,7 +379,7 @@ def main():
     roof = roofline_of(gq, plan, psi, n, min(K, 200), peak)
     roof["floor_frac"] = round(floor_frac, 4)
     roof["peak_source"] = peak_src
-    roof["sweeps_per_step"] = 4
+    roof["sweeps_per_step"] = 2 if plan.sweep_variant(n, 1, 7) == 0 else 4   # HBM passes of the field
 
     # end to end through the public C ABI with host buffers
     host = torch.empty((n, n, n), dtype=torch.complex64).pin_memory()

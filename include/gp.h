@@ -190,16 +190,31 @@ int gp_profile_read(gp_plan* plan, int max_kinds, char* names, long long* launch
 /* Number of kernels this plan has launched (or replayed inside graphs) since creation. */
 long long gp_launch_count(const gp_plan* plan);
 
-/* Autotuner of the float32 sweep kernels (no counterpart in the paper).  For every grid length
- * of the plan's float32 fields and every sweep of its time step (z: inverse/N/forward variants,
- * y: forward and inverse, x: forward, K, inverse) it times the candidate kernels on a scratch
- * field (allocated and freed here) and keeps the fastest: 0 the TMA-pipelined persistent kernel
- * at full occupancy, 1 the same with one CTA per SM, 2 the non-persistent kernel.  cache_path
- * (NULL: none) names a JSON file of earlier choices keyed by GPU name, length, axis and operation;
- * cached choices are reused without timing and new ones are added.  Synchronises the stream and
- * drops captured graphs.  gp_plan_sweep_variant returns the variant in use for a sweep kind. */
+/* Autotuner of the float32 sweep kernels (no counterpart in the paper).  A sweep kind is
+ * (axis, op): axis 0 = x, 1 = y, 2 = z; op 1 forward, 2 inverse, 3 inverse-N-forward,
+ * 4 N-forward, 5 inverse-N, 6 forward-K-inverse (x only), and 7 = the fused plane kernel that
+ * performs forward y, x (forward, K, inverse) and inverse y of every z-plane in one launch
+ * (axis 1).  For every grid length of the plan's float32 fields and every kind of its time step
+ * the tuner times the candidates on a scratch field (allocated and freed here) and keeps the
+ * fastest: 0 the TMA-pipelined persistent kernel at full occupancy, 1 the same with one CTA per
+ * SM, 2 the non-persistent kernel, 3 (y and z only) the TMA kernel with two shared-memory stages;
+ * for op 7, 0 = the fused kernel and 2 = the three separate sweeps with their own variants.  cache_path (NULL: none) names a JSON file of earlier
+ * choices keyed by GPU name, length, axis and op; cached choices are reused without timing and
+ * new ones are added.  Synchronises the stream and drops captured graphs.
+ * gp_plan_sweep_variant returns the variant in use for a kind (default 0: fused plane kernel
+ * and TMA sweeps wherever the length has them).  gp_plan_set_sweep_variant sets it by hand
+ * (GP_ERR_INVALID_ARG for an unknown kind or variant); it synchronises the stream and drops
+ * captured graphs. */
 gp_status gp_plan_autotune(gp_plan* plan, const char* cache_path);
 int gp_plan_sweep_variant(gp_plan* plan, int n, int axis, int op);
+gp_status gp_plan_set_sweep_variant(gp_plan* plan, int n, int axis, int op, int variant);
+
+/* Waits for the plan's stream and reads the device status word that the persistent sweep
+ * kernels set when one of their bounded waits (a TMA copy, a tile counter of the fused plane
+ * kernel) gives up instead of hanging.  GP_OK if none did since the last check; otherwise
+ * GP_ERR_TIMEOUT (the fields written since then are invalid) and the word is cleared.
+ * gp_step_host and gp_diagnostics perform the same check. */
+gp_status gp_plan_sync(gp_plan* plan);
 
 /* Message of the last failed call on this plan ("" if none); valid until the next call. */
 const char* gp_last_error(const gp_plan* plan);

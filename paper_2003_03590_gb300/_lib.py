@@ -10,6 +10,9 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_INVALID_ARG", 2: "GP_ERR_UNSUPPORTED_SIZE", 3: 
           4: "GP_ERR_CUDA", 5: "GP_ERR_TIMEOUT", 6: "GP_ERR_NONFINITE"}
 GP_FP32, GP_FP64 = 0, 1
 GP_SPLIT_NKN, GP_SPLIT_KNK = 0, 1
+# sweep kinds (axis, op) and kernel variants of gp_plan_sweep_variant / gp_plan_set_sweep_variant
+OP_FWD, OP_INV, OP_INV_N_FWD, OP_N_FWD, OP_INV_N, OP_FWD_K_INV, OP_PLANE = 1, 2, 3, 4, 5, 6, 7
+VARIANT_TMA, VARIANT_TMA_ONE, VARIANT_PLAIN, VARIANT_TMA_2STAGE = 0, 1, 2, 3
 SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024)
 
 
@@ -49,6 +52,8 @@ SIGNATURES = {
     "gp_diagnostics_noalloc": (_I, [_I, _D, _D, _P, ctypes.POINTER(Diag), ctypes.POINTER(_D), _I, _P]),
     "gp_plan_autotune": (_I, [_P, ctypes.c_char_p]),
     "gp_plan_sweep_variant": (_I, [_P, _I, _I, _I]),
+    "gp_plan_set_sweep_variant": (_I, [_P, _I, _I, _I, _I]),
+    "gp_plan_sync": (_I, [_P]),
     "gp_profile": (_I, [_P, _I]),
     "gp_profile_read": (_I, [_P, _I, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)]),
     "gp_launch_count": (ctypes.c_longlong, [_P]),

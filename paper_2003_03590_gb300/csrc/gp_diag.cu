@@ -252,6 +252,10 @@ static gp_status diag_impl(gp_plan* p, int field, const cpx<T>* psi, gp_diag* ou
   GP_CUDA(p, cudaMemcpyAsync(&flag, p->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   GP_CUDA(p, cudaMemcpyAsync(hs.data(), spec, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   GP_CUDA(p, cudaStreamSynchronize(s));
+  {
+    gp_status st = check_status(p);   // a sweep that gave up a bounded wait since the last check
+    if (st != GP_OK) return st;
+  }
   if (flag) return fail(p, GP_ERR_NONFINITE, "gp_diagnostics: field holds NaN or Inf");
   const double dn = (double)npts, dn2 = dn * dn;
   gp_diag d{};

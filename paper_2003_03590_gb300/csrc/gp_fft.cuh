@@ -308,27 +308,33 @@ template <int L, bool INV> __device__ __forceinline__ int out_pos(int e, int t) 
 // Uses shared memory for the exchanges between passes (two barriers each).  WARP_X: every
 // pencil's threads lie in one warp and its exchange region is private to it, so the
 // exchanges only need warp-level barriers.
-template <bool WARP_X> __device__ __forceinline__ void xsync() {
-  if constexpr (WARP_X) __syncwarp();
-  else __syncthreads();
+// NB: 0 = the block barrier; otherwise named barrier 1 over the first NB threads (kernels
+// whose last warp does other work than the transforms).
+template <int NB> __device__ __forceinline__ void bsync() {
+  if constexpr (NB == 0) __syncthreads();
+  else asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
 }
-template <typename T, int L, int B, class Lay, bool INV, bool WARP_X = false, bool TW_SH = false>
+template <bool WARP_X, int NB = 0> __device__ __forceinline__ void xsync() {
+  if constexpr (WARP_X) __syncwarp();
+  else bsync<NB>();
+}
+template <typename T, int L, int B, class Lay, bool INV, bool WARP_X = false, bool TW_SH = false, int NB = 0>
 __device__ __forceinline__ void fft_regs(cpx<T>* v, int t, int p, cpx<T>* sm, const Lay& lay,
                                          const tw_t<T>* __restrict__ tw) {
   constexpr int NP = Plan<L>::NP;
   pass_compute<T, L, B, Lay, INV, 0, TW_SH>(v, t, tw);
   if constexpr (NP > 1) {
     pass_store<T, L, Lay, INV, 0>(v, t, p, sm, lay);
-    xsync<WARP_X>();
+    xsync<WARP_X, NB>();
     pass_load<T, L, Lay, INV, 1>(v, t, p, sm, lay);
-    xsync<WARP_X>();
+    xsync<WARP_X, NB>();
     pass_compute<T, L, B, Lay, INV, 1, TW_SH>(v, t, tw);
   }
   if constexpr (NP > 2) {
     pass_store<T, L, Lay, INV, 1>(v, t, p, sm, lay);
-    xsync<WARP_X>();
+    xsync<WARP_X, NB>();
     pass_load<T, L, Lay, INV, 2>(v, t, p, sm, lay);
-    xsync<WARP_X>();
+    xsync<WARP_X, NB>();
     pass_compute<T, L, B, Lay, INV, 2, TW_SH>(v, t, tw);
   }
 }

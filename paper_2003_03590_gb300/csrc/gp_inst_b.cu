@@ -1,6 +1,6 @@
 // Instantiations of the pencil sweeps for some grid lengths (compiled in parallel).
 #include "gp_internal.h"
-#include "gp_tma.cuh"
+#include "gp_plane.cuh"
 
 namespace gp {
 cudaError_t sweep_f32_64(const SweepArgs<float>& a, cudaStream_t s) { return SweepLaunch<float, 64>::launch(a, s); }
@@ -11,10 +11,46 @@ cudaError_t sweep_f32_128(const SweepArgs<float>& a, cudaStream_t s) { return Sw
 cudaError_t sweep_f64_128(const SweepArgs<double>& a, cudaStream_t s) { return SweepLaunch<double, 128>::launch(a, s); }
 cudaError_t sweep_f32_192(const SweepArgs<float>& a, cudaStream_t s) { return SweepLaunch<float, 192>::launch(a, s); }
 cudaError_t sweep_f64_192(const SweepArgs<double>& a, cudaStream_t s) { return SweepLaunch<double, 192>::launch(a, s); }
-cudaError_t tma_sweep_32(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<32>::launch(a, ctas, s); }
-cudaError_t tma_sweep_48(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<48>::launch(a, ctas, s); }
-cudaError_t tma_sweep_64(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<64>::launch(a, ctas, s); }
-cudaError_t tma_sweep_96(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<96>::launch(a, ctas, s); }
-cudaError_t tma_sweep_128(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<128>::launch(a, ctas, s); }
-cudaError_t tma_sweep_192(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<192>::launch(a, ctas, s); }
+cudaError_t tma_sweep_32(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
+  return TmaLaunch<32>::launch(a, ctas, stages, s);
+}
+cudaError_t tma_plane_32(TmaPlaneArgs& a, cudaStream_t s) {
+  a.lag = TmaPlaneLaunch<32>::lag(TmaPlaneLaunch<32>::grid(a.count));
+  return TmaPlaneLaunch<32>::launch(a, s);
+}
+cudaError_t tma_sweep_48(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
+  return TmaLaunch<48>::launch(a, ctas, stages, s);
+}
+cudaError_t tma_plane_48(TmaPlaneArgs& a, cudaStream_t s) {
+  a.lag = TmaPlaneLaunch<48>::lag(TmaPlaneLaunch<48>::grid(a.count));
+  return TmaPlaneLaunch<48>::launch(a, s);
+}
+cudaError_t tma_sweep_64(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
+  return TmaLaunch<64>::launch(a, ctas, stages, s);
+}
+cudaError_t tma_plane_64(TmaPlaneArgs& a, cudaStream_t s) {
+  a.lag = TmaPlaneLaunch<64>::lag(TmaPlaneLaunch<64>::grid(a.count));
+  return TmaPlaneLaunch<64>::launch(a, s);
+}
+cudaError_t tma_sweep_96(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
+  return TmaLaunch<96>::launch(a, ctas, stages, s);
+}
+cudaError_t tma_plane_96(TmaPlaneArgs& a, cudaStream_t s) {
+  a.lag = TmaPlaneLaunch<96>::lag(TmaPlaneLaunch<96>::grid(a.count));
+  return TmaPlaneLaunch<96>::launch(a, s);
+}
+cudaError_t tma_sweep_128(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
+  return TmaLaunch<128>::launch(a, ctas, stages, s);
+}
+cudaError_t tma_plane_128(TmaPlaneArgs& a, cudaStream_t s) {
+  a.lag = TmaPlaneLaunch<128>::lag(TmaPlaneLaunch<128>::grid(a.count));
+  return TmaPlaneLaunch<128>::launch(a, s);
+}
+cudaError_t tma_sweep_192(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
+  return TmaLaunch<192>::launch(a, ctas, stages, s);
+}
+cudaError_t tma_plane_192(TmaPlaneArgs& a, cudaStream_t s) {
+  a.lag = TmaPlaneLaunch<192>::lag(TmaPlaneLaunch<192>::grid(a.count));
+  return TmaPlaneLaunch<192>::launch(a, s);
+}
 }  // namespace gp

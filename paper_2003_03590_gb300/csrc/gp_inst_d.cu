@@ -1,9 +1,15 @@
 // Instantiations of the pencil sweeps for some grid lengths (compiled in parallel).
 #include "gp_internal.h"
-#include "gp_tma.cuh"
+#include "gp_plane.cuh"
 
 namespace gp {
 cudaError_t sweep_f32_512(const SweepArgs<float>& a, cudaStream_t s) { return SweepLaunch<float, 512>::launch(a, s); }
 cudaError_t sweep_f64_512(const SweepArgs<double>& a, cudaStream_t s) { return SweepLaunch<double, 512>::launch(a, s); }
-cudaError_t tma_sweep_512(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<512>::launch(a, ctas, s); }
+cudaError_t tma_sweep_512(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
+  return TmaLaunch<512>::launch(a, ctas, stages, s);
+}
+cudaError_t tma_plane_512(TmaPlaneArgs& a, cudaStream_t s) {
+  a.lag = TmaPlaneLaunch<512>::lag(TmaPlaneLaunch<512>::grid(a.count));
+  return TmaPlaneLaunch<512>::launch(a, s);
+}
 }  // namespace gp

@@ -1,9 +1,15 @@
 // Instantiations of the pencil sweeps for some grid lengths (compiled in parallel).
 #include "gp_internal.h"
-#include "gp_tma.cuh"
+#include "gp_plane.cuh"
 
 namespace gp {
 cudaError_t sweep_f32_1024(const SweepArgs<float>& a, cudaStream_t s) { return SweepLaunch<float, 1024>::launch(a, s); }
 cudaError_t sweep_f64_1024(const SweepArgs<double>& a, cudaStream_t s) { return SweepLaunch<double, 1024>::launch(a, s); }
-cudaError_t tma_sweep_1024(const TmaSweepArgs& a, int ctas, cudaStream_t s) { return TmaLaunch<1024>::launch(a, ctas, s); }
+cudaError_t tma_sweep_1024(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
+  return TmaLaunch<1024>::launch(a, ctas, stages, s);
+}
+cudaError_t tma_plane_1024(TmaPlaneArgs& a, cudaStream_t s) {
+  a.lag = TmaPlaneLaunch<1024>::lag(TmaPlaneLaunch<1024>::grid(a.count));
+  return TmaPlaneLaunch<1024>::launch(a, s);
+}
 }  // namespace gp

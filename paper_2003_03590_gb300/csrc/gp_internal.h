@@ -19,13 +19,21 @@ GP_SIZES(GP_DECL_SWEEP)
 
 #define GP_TMA_SIZES(X) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(512) X(1024)
 struct TmaSweepArgs;
-#define GP_DECL_TMA(L) cudaError_t tma_sweep_##L(const TmaSweepArgs&, int, cudaStream_t);
+struct TmaPlaneArgs;
+#define GP_DECL_TMA(L)                                                     \
+  cudaError_t tma_sweep_##L(const TmaSweepArgs&, int, int, cudaStream_t);   \
+  cudaError_t tma_plane_##L(TmaPlaneArgs&, cudaStream_t);
 GP_TMA_SIZES(GP_DECL_TMA)
 #undef GP_DECL_TMA
 bool tma_supported(int n);
 // launch one TMA sweep for the fields psi[0..count) of length n (float32 fused path)
 cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* status, cudaStream_t s,
-                      int ctas_req = 0);   // CTAs per SM; 0: as many as fit
+                      int ctas_req = 0,    // CTAs per SM; 0: as many as fit
+                      int stages = 3);     // shared-memory stages of the y/z kernels: 3 or 2
+// launch the fused plane kernel (forward y, forward x + K + inverse x, inverse y) for the
+// fields psi[0..count) of length n; sync: device ints, at least plane_sync_ints(n, count)
+cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* sync, int* status, cudaStream_t s);
+inline size_t plane_sync_ints(int n, int count) { return 1 + 2 * (size_t)n * (size_t)count; }
 
 bool supported_n(int n);
 void split_hilo(double v, float* hi, float* lo);   // see gp_plan.cu
@@ -78,6 +86,8 @@ struct gp_plan {
   long long launches = 0;                  // kernels launched or replayed
   bool use_tma = true;                     // float32 sweeps through the TMA-pipelined kernels
   std::vector<std::pair<long long, int>> tune;   // (n, axis, op) key -> sweep variant (gp_plan_autotune)
+  int* plane_sync = nullptr;               // counters of the fused plane kernel
+  size_t plane_sync_ints = 0;
   bool prof = false;                       // per-launch event timing (gp_profile)
   std::vector<cudaEvent_t> ev_pool;        // recorded events, two per profiled launch
   std::vector<int> ev_kind;                // kind index of each profiled launch
@@ -88,6 +98,8 @@ namespace gp {
 
 gp_status fail(gp_plan* p, gp_status st, const std::string& msg);
 gp_status cuda_fail(gp_plan* p, cudaError_t e, const char* what);
+// synchronise the plan's stream and report (and clear) the sweep kernels' status word
+gp_status check_status(gp_plan* p);
 #define GP_CUDA(p, call)                                   \
   do {                                                     \
     cudaError_t e_ = (call);                               \
@@ -108,6 +120,17 @@ template <typename T> cudaError_t launch_nonlinear(cpx<T>* psi, long long npts, 
 template <typename T> cudaError_t launch_kinetic_mul(cpx<T>* psi, int n, const cpx<T>* ek, cudaStream_t s);
 template <typename T> cudaError_t launch_vjp_nonlinear(const cpx<T>* psi_in, cpx<T>* lam, long long npts, double coef,
                                                        double shift, cudaStream_t s);
+
+// sweep variants (gp_step.cu): 0 TMA persistent, 1 TMA one CTA per SM, 2 plain, 3 TMA with two
+// stages (y and z only); for OP_PLANE 0 means the fused plane kernel and 2 the three separate
+// sweeps it replaces
+enum { VARIANT_TMA = 0, VARIANT_TMA_ONE = 1, VARIANT_PLAIN = 2, VARIANT_TMA_2STAGE = 3 };
+int sweep_variant(gp_plan* p, int n, int axis, int op);
+bool plane_on(gp_plan* p, int n);
+gp_status ensure_plane_sync(gp_plan* p, size_t ints);
+// one float32 sweep of the given kind with the given variant (used by the autotuner)
+cudaError_t launch_sweep_variant(gp_plan* p, int n, const SweepArgs<float>& a, void* const* psi, int variant,
+                                 cudaStream_t s);
 
 // the time step (gp_step.cu): advance one field by nsteps on the plan's stream
 gp_status step_field(gp_plan* p, int field, void* psi, int nsteps);

@@ -60,6 +60,17 @@ gp_status fail(gp_plan* p, gp_status st, const std::string& msg) {
   if (p) p->err = msg;
   return st;
 }
+
+gp_status check_status(gp_plan* p) {
+  GP_CUDA(p, p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+  int st = 0;
+  GP_CUDA(p, cudaMemcpy(&st, p->flag + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    GP_CUDA(p, cudaMemset(p->flag + 1, 0, sizeof(int)));
+    return fail(p, GP_ERR_TIMEOUT, "a bounded wait in a sweep kernel gave up: fields written since the last check are invalid");
+  }
+  return GP_OK;
+}
 gp_status cuda_fail(gp_plan* p, cudaError_t e, const char* what) {
   std::string m = std::string(what) + ": " + cudaGetErrorString(e);
   return fail(p, e == cudaErrorMemoryAllocation ? GP_ERR_OOM : GP_ERR_CUDA, m);
@@ -335,6 +346,11 @@ gp_status gp_plan_create(const gp_field_params* fields, int nfields, void* strea
   return GP_OK;
 }
 
+gp_status gp_plan_sync(gp_plan* p) {
+  if (!p) return GP_ERR_INVALID_ARG;
+  return gp::check_status(p);
+}
+
 gp_status gp_plan_destroy(gp_plan* p) {
   if (!p) return GP_OK;
   if (p->stream) cudaStreamSynchronize(p->stream);
@@ -343,6 +359,7 @@ gp_status gp_plan_destroy(gp_plan* p) {
   if (p->acc) cudaFree(p->acc);
   if (p->flag) cudaFree(p->flag);
   if (p->adj_ws) cudaFree(p->adj_ws);
+  if (p->plane_sync) cudaFree(p->plane_sync);
   if (p->cycle_graph) cudaGraphExecDestroy(p->cycle_graph);
   if (p->run_graph) cudaGraphExecDestroy(p->run_graph);
   delete p;

@@ -23,9 +23,6 @@
 
 namespace gp {
 
-// sweep variants the autotuner chooses between
-enum { VARIANT_TMA = 0, VARIANT_TMA_ONE = 1, VARIANT_PLAIN = 2 };
-
 static long long tune_key(int n, int axis, int op) { return (long long)n * 64 + axis * 8 + op; }
 
 int sweep_variant(gp_plan* p, int n, int axis, int op) {
@@ -34,6 +31,44 @@ int sweep_variant(gp_plan* p, int n, int axis, int op) {
   for (const auto& e : p->tune)
     if (e.first == k) return e.second;
   return VARIANT_TMA;
+}
+
+// forward y, x (forward, K, inverse) and inverse y of a step as one fused plane-kernel launch
+bool plane_on(gp_plan* p, int n) { return sweep_variant(p, n, 1, OP_PLANE) == VARIANT_TMA; }
+
+gp_status ensure_plane_sync(gp_plan* p, size_t ints) {
+  if (p->plane_sync_ints >= ints) return GP_OK;
+  if (p->plane_sync) {
+    GP_CUDA(p, p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+    cudaFree(p->plane_sync);
+    p->plane_sync = nullptr;
+    p->plane_sync_ints = 0;
+  }
+  if (cudaMalloc(&p->plane_sync, ints * sizeof(int)) != cudaSuccess) {
+    p->plane_sync = nullptr;
+    return fail(p, GP_ERR_OOM, "plane kernel counters");
+  }
+  p->plane_sync_ints = ints;
+  return GP_OK;
+}
+
+cudaError_t launch_sweep_variant(gp_plan* p, int n, const SweepArgs<float>& a, void* const* psi, int variant,
+                                 cudaStream_t s) {
+  if (a.op == OP_PLANE) {
+    if (variant == VARIANT_TMA) return tma_plane(n, a, psi, p->plane_sync, p->flag + 1, s);
+    SweepArgs<float> b = a;
+    const int ops[3][2] = {{1, OP_FWD}, {0, OP_FWD_K_INV}, {1, OP_INV}};
+    for (const auto& o : ops) {
+      b.axis = o[0];
+      b.op = o[1];
+      cudaError_t e = launch_sweep_variant(p, n, b, psi, sweep_variant(p, n, b.axis, b.op), s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  if (variant == VARIANT_PLAIN) return sweep(n, a, s);
+  if (variant == VARIANT_TMA_2STAGE && a.axis != 0) return tma_sweep(n, a, psi, p->flag + 1, s, 0, 2);
+  return tma_sweep(n, a, psi, p->flag + 1, s, variant == VARIANT_TMA_ONE ? 1 : 0);
 }
 
 namespace {
@@ -93,7 +128,7 @@ gp_status launch_item(gp_plan* p, const Group& G, const Item& it, void* const* p
   a.axis = it.axis;
   a.nl_coef = (float)(F.beta * it.s_nl);
   a.nl_shift = F.prm.nonlin_minus_one ? 1.0f : 0.0f;
-  if (it.op == OP_FWD_K_INV) {
+  if (it.op == OP_FWD_K_INV || it.op == OP_PLANE) {
     const float4* kt = (const float4*)ktable(p, G.fields[0], it.s_k, false);
     if (!kt) return fail(p, GP_ERR_OOM, "kinetic table allocation");
     a.ekx = kt;
@@ -102,11 +137,12 @@ gp_status launch_item(gp_plan* p, const Group& G, const Item& it, void* const* p
   a.scale_inv = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (p->prof) {
-    static const char* opn[] = {"", "fwd", "inv", "inv_n_fwd", "n_fwd", "inv_n", "fwd_k_inv"};
+    static const char* opn[] = {"", "fwd", "inv", "inv_n_fwd", "n_fwd", "inv_n", "fwd_k_inv", "fwd_k_inv"};
     const bool tma = sweep_variant(p, G.n, it.axis, it.op) != VARIANT_PLAIN;
-    std::string name = std::string(tma ? (it.axis == 0 ? "k_tma_contig<" : "k_tma_strided<")
-                                       : (it.axis == 0 ? "k_sweep_contig<float," : "k_sweep_strided<float,")) +
-                       std::to_string(G.n) + ">:" + opn[it.op] + ":" + "xyz"[it.axis];
+    std::string name = it.op == OP_PLANE ? std::string("k_tma_plane<") + std::to_string(G.n) + ">:y_fwd_x_fwd_k_inv_y_inv:xy"
+                       : std::string(tma ? (it.axis == 0 ? "k_tma_contig<" : "k_tma_strided<")
+                                         : (it.axis == 0 ? "k_sweep_contig<float," : "k_sweep_strided<float,")) +
+                             std::to_string(G.n) + ">:" + opn[it.op] + ":" + "xyz"[it.axis];
     int kind = -1;
     for (int q = 0; q < (int)p->kinds.size(); ++q)
       if (p->kinds[q] == name) kind = q;
@@ -121,23 +157,22 @@ gp_status launch_item(gp_plan* p, const Group& G, const Item& it, void* const* p
     p->ev_pool.push_back(e1);
     p->ev_kind.push_back(kind);
   }
-  cudaError_t e;
-  const int variant = sweep_variant(p, G.n, it.axis, it.op);
-  if (variant != VARIANT_PLAIN) {
-    void* ptrs[GP_MAXB];
-    for (int k = 0; k < a.count; ++k) ptrs[k] = psi[G.fields[k]];
-    e = tma_sweep(G.n, a, ptrs, p->flag + 1, s, variant == VARIANT_TMA_ONE ? 1 : 0);
-  } else {
-    e = sweep(G.n, a, s);
-  }
+  void* ptrs[GP_MAXB];
+  for (int k = 0; k < a.count; ++k) ptrs[k] = psi[G.fields[k]];
+  cudaError_t e = launch_sweep_variant(p, G.n, a, ptrs, sweep_variant(p, G.n, it.axis, it.op), s);
   if (e != cudaSuccess) return cuda_fail(p, e, "sweep launch");
   if (p->prof) GP_CUDA(p, cudaEventRecord(e1, s));
   p->launches += 1;
   return GP_OK;
 }
 
-// the four sweeps that carry K(sk) and then N(sn) to the next cycle
-void k_block(std::vector<Item>& v, int g, double sk) {
+// the sweeps that carry K(sk): forward y, x (forward, K, inverse), inverse y -- three launches,
+// or one of the fused plane kernel
+void k_block(std::vector<Item>& v, int g, double sk, bool plane) {
+  if (plane) {
+    v.push_back({g, 1, OP_PLANE, 0.0, sk});
+    return;
+  }
   v.push_back({g, 1, OP_FWD, 0.0, 0.0});
   v.push_back({g, 0, OP_FWD_K_INV, 0.0, sk});
   v.push_back({g, 1, OP_INV, 0.0, 0.0});
@@ -238,6 +273,10 @@ gp_status step_all(gp_plan* p, void* const* psi, int nsteps) {
     const FieldPlan& F = p->f[G.fields[0]];
     if (!ktable(p, G.fields[0], F.prm.dt, false) || !ktable(p, G.fields[0], 0.5 * F.prm.dt, false))
       return fail(p, GP_ERR_OOM, "kinetic table allocation");
+    if (plane_on(p, G.n)) {
+      gp_status st = ensure_plane_sync(p, plane_sync_ints(G.n, (int)G.fields.size()));
+      if (st != GP_OK) return st;
+    }
   }
   if (!any32) return GP_OK;
 
@@ -246,19 +285,20 @@ gp_status step_all(gp_plan* p, void* const* psi, int nsteps) {
     const Group& G = groups[g];
     if (G.fp64) continue;
     const double dt = p->f[G.fields[0]].prm.dt, h = 0.5 * dt;
+    const bool pl = plane_on(p, G.n);
     if (G.split == GP_SPLIT_NKN) {
       pro.push_back({g, 2, OP_N_FWD, h, 0.0});
-      k_block(pro, g, dt);
+      k_block(pro, g, dt, pl);
       epi.push_back({g, 2, OP_INV_N, h, 0.0});
     } else {
       pro.push_back({g, 2, OP_FWD, 0.0, 0.0});
-      k_block(pro, g, h);
+      k_block(pro, g, h, pl);
       tail.push_back({g, 2, OP_INV_N_FWD, dt, 0.0});
-      k_block(tail, g, h);
+      k_block(tail, g, h, pl);
       epi.push_back({g, 2, OP_INV, 0.0, 0.0});
     }
     cyc.push_back({g, 2, OP_INV_N_FWD, dt, 0.0});
-    k_block(cyc, g, dt);
+    k_block(cyc, g, dt, pl);
   }
   const int ncycles = nsteps - 1;
 
@@ -327,21 +367,26 @@ gp_status step_field(gp_plan* p, int field, void* psi, int nsteps) {
   G.split = F.prm.split;
   std::vector<Group> groups{G};
   const double dt = F.prm.dt, h = 0.5 * dt;
+  const bool pl = plane_on(p, G.n);
+  if (pl) {
+    gp_status st = ensure_plane_sync(p, plane_sync_ints(G.n, 1));
+    if (st != GP_OK) return st;
+  }
   std::vector<Item> items;
   if (G.split == GP_SPLIT_NKN) {
     items.push_back({0, 2, OP_N_FWD, h, 0.0});
-    k_block(items, 0, dt);
+    k_block(items, 0, dt, pl);
     for (int c = 0; c < nsteps - 1; ++c) {
       items.push_back({0, 2, OP_INV_N_FWD, dt, 0.0});
-      k_block(items, 0, dt);
+      k_block(items, 0, dt, pl);
     }
     items.push_back({0, 2, OP_INV_N, h, 0.0});
   } else {
     items.push_back({0, 2, OP_FWD, 0.0, 0.0});
-    k_block(items, 0, h);
+    k_block(items, 0, h, pl);
     for (int c = 0; c < nsteps; ++c) {
       items.push_back({0, 2, OP_INV_N_FWD, dt, 0.0});
-      k_block(items, 0, c == nsteps - 1 ? h : dt);
+      k_block(items, 0, c == nsteps - 1 ? h : dt, pl);
     }
     items.push_back({0, 2, OP_INV, 0.0, 0.0});
   }
@@ -381,8 +426,7 @@ gp_status gp_step_host(gp_plan* p, void* const* psi_host, int nsteps) {
     const size_t bytes = (size_t)F.npts * (F.fp64 ? 16 : 8);
     GP_CUDA(p, cudaMemcpyAsync(psi_host[i], F.host_buf, bytes, cudaMemcpyDeviceToHost, p->stream));
   }
-  GP_CUDA(p, cudaStreamSynchronize(p->stream));
-  return GP_OK;
+  return check_status(p);
 }
 
 }  // extern "C"

@@ -19,7 +19,8 @@
 
 namespace gp {
 
-enum SweepOp : int { OP_FWD = 1, OP_INV = 2, OP_INV_N_FWD = 3, OP_N_FWD = 4, OP_INV_N = 5, OP_FWD_K_INV = 6 };
+enum SweepOp : int { OP_FWD = 1, OP_INV = 2, OP_INV_N_FWD = 3, OP_N_FWD = 4, OP_INV_N = 5, OP_FWD_K_INV = 6,
+                     OP_PLANE = 7 };   // OP_PLANE: forward y, OP_FWD_K_INV along x, inverse y (gp_plane.cuh)
 
 constexpr int GP_MAXB = 32;  // fields of one shape handled by one launch (blockIdx.y)
 
@@ -118,85 +119,75 @@ __device__ __forceinline__ void store_pattern(const cpx<T>* v, int t, const GetA
 // TILE_IN_SMEM: the tile addressed by addr() lives in the same shared memory that the
 // passes use for their exchanges, so the block synchronises after reading it (and, with
 // warp-private exchanges, before writing it back).  WARP_X: see fft_regs.
-template <typename T, int L, int B, class Lay, class GetAddr, bool TILE_IN_SMEM = false, bool WARP_X = false,
-          bool TW_SH = false>
-__device__ __forceinline__ void sweep_body(const SweepArgs<T>& a, int t, int p, cpx<T>* sm, const Lay& lay,
-                                           const GetAddr& addr, int i1, int i2) {
+template <int OP, typename T, int L, int B, class Lay, class GetAddr, bool TILE_IN_SMEM = false, bool WARP_X = false,
+          bool TW_SH = false, int NB = 0>
+__device__ __forceinline__ void sweep_op_body(const SweepArgs<T>& a, int t, int p, cpx<T>* sm, const Lay& lay,
+                                              const GetAddr& addr, int i1, int i2) {
   using V = cpx<T>;
   constexpr int E = Plan<L>::E;
   constexpr KConst inv_l = kconst(1.0 / L);
+  constexpr bool IN_INV = OP == OP_INV || OP == OP_INV_N || OP == OP_INV_N_FWD;
+  constexpr bool OUT_INV = OP == OP_INV || OP == OP_INV_N || OP == OP_FWD_K_INV;
   const bool sc = a.scale_inv != 0;
   V v[E];
-  switch (a.op) {
-    case OP_FWD:
-      load_pattern<T, L, false>(v, t, addr);
-      if constexpr (TILE_IN_SMEM) __syncthreads();
-      fft_regs<T, L, B, Lay, false, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_fwd);
-      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
-      store_pattern<T, L, false>(v, t, addr);
-      break;
-    case OP_INV:
-      load_pattern<T, L, true>(v, t, addr);
-      if constexpr (TILE_IN_SMEM) __syncthreads();
-      fft_regs<T, L, B, Lay, true, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_inv);
+  load_pattern<T, L, IN_INV>(v, t, addr);
+  if constexpr (TILE_IN_SMEM) bsync<NB>();
+  if constexpr (OP == OP_N_FWD) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = nonlinear(v[e], a.nl_coef, a.nl_shift);
+  }
+  if constexpr (OP == OP_FWD || OP == OP_N_FWD || OP == OP_FWD_K_INV)
+    fft_regs<T, L, B, Lay, false, WARP_X, TW_SH, NB>(v, t, p, sm, lay, a.tw_fwd);
+  if constexpr (IN_INV) {
+    fft_regs<T, L, B, Lay, true, WARP_X, TW_SH, NB>(v, t, p, sm, lay, a.tw_inv);
+    if constexpr (OP == OP_INV) {
       if (sc) {
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = kscale(v[e], inv_l);
       }
-      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
-      store_pattern<T, L, true>(v, t, addr);
-      break;
-    case OP_N_FWD:
-      load_pattern<T, L, false>(v, t, addr);
-      if constexpr (TILE_IN_SMEM) __syncthreads();
-#pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = nonlinear(v[e], a.nl_coef, a.nl_shift);
-      fft_regs<T, L, B, Lay, false, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_fwd);
-      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
-      store_pattern<T, L, false>(v, t, addr);
-      break;
-    case OP_INV_N:
-      load_pattern<T, L, true>(v, t, addr);
-      if constexpr (TILE_IN_SMEM) __syncthreads();
-      fft_regs<T, L, B, Lay, true, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_inv);
+    } else {
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = nonlinear(sc ? kscale(v[e], inv_l) : v[e], a.nl_coef, a.nl_shift);
-      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
-      store_pattern<T, L, true>(v, t, addr);
-      break;
-    case OP_INV_N_FWD:
-      load_pattern<T, L, true>(v, t, addr);
-      if constexpr (TILE_IN_SMEM) __syncthreads();
-      fft_regs<T, L, B, Lay, true, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_inv);
+    }
+  }
+  if constexpr (OP == OP_INV_N_FWD) {
+    xsync<WARP_X, NB>();  // shared memory is reused by the forward passes
+    fft_regs<T, L, B, Lay, false, WARP_X, TW_SH, NB>(v, t, p, sm, lay, a.tw_fwd);
+  }
+  if constexpr (OP == OP_FWD_K_INV) {
+    if constexpr (sizeof(T) == 4) {
+      // two products by factors exact to float64 (hi + lo), each rounded once: the magnitude
+      // of the field is not biased by the kinetic factor, which is the same for a given k in
+      // every step
+      const float4 eo = __ldg(a.ek2 + i2 * L + i1);
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = nonlinear(sc ? kscale(v[e], inv_l) : v[e], a.nl_coef, a.nl_shift);
-      xsync<WARP_X>();  // shared memory is reused by the forward passes
-      fft_regs<T, L, B, Lay, false, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_fwd);
-      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
-      store_pattern<T, L, false>(v, t, addr);
-      break;
-    case OP_FWD_K_INV:
-      load_pattern<T, L, false>(v, t, addr);
-      if constexpr (TILE_IN_SMEM) __syncthreads();
-      fft_regs<T, L, B, Lay, false, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_fwd);
+      for (int e = 0; e < E; ++e) v[e] = twmul(twmul(v[e], __ldg(a.ekx + out_pos<L, false>(e, t))), eo);
+    } else {
+      const V eo = cmul(__ldg(a.ek + i1), __ldg(a.ek + i2));
 #pragma unroll
-      if constexpr (sizeof(T) == 4) {
-        // two products by factors exact to float64 (hi + lo), each rounded once: the magnitude
-        // of the field is not biased by the kinetic factor, which is the same for a given k in
-        // every step
-        const float4 eo = __ldg(a.ek2 + i2 * L + i1);
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = twmul(twmul(v[e], __ldg(a.ekx + out_pos<L, false>(e, t))), eo);
-      } else {
-        const V eo = cmul(__ldg(a.ek + i1), __ldg(a.ek + i2));
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = kinetic_apply(v[e], eo, __ldg(a.ek + out_pos<L, false>(e, t)), a.k_norm);
-      }
-      xsync<WARP_X>();
-      fft_regs<T, L, B, Lay, true, WARP_X, TW_SH>(v, t, p, sm, lay, a.tw_inv);
-      if constexpr (TILE_IN_SMEM && WARP_X) __syncthreads();
-      store_pattern<T, L, true>(v, t, addr);
-      break;
+      for (int e = 0; e < E; ++e) v[e] = kinetic_apply(v[e], eo, __ldg(a.ek + out_pos<L, false>(e, t)), a.k_norm);
+    }
+    xsync<WARP_X, NB>();
+    fft_regs<T, L, B, Lay, true, WARP_X, TW_SH, NB>(v, t, p, sm, lay, a.tw_inv);
+  }
+  if constexpr (TILE_IN_SMEM && WARP_X) bsync<NB>();
+  store_pattern<T, L, OUT_INV>(v, t, addr);
+}
+
+template <typename T, int L, int B, class Lay, class GetAddr, bool TILE_IN_SMEM = false, bool WARP_X = false,
+          bool TW_SH = false>
+__device__ __forceinline__ void sweep_body(const SweepArgs<T>& a, int t, int p, cpx<T>* sm, const Lay& lay,
+                                           const GetAddr& addr, int i1, int i2) {
+  switch (a.op) {
+#define GP_OP_CASE(OPV) \
+  case OPV: sweep_op_body<OPV, T, L, B, Lay, GetAddr, TILE_IN_SMEM, WARP_X, TW_SH>(a, t, p, sm, lay, addr, i1, i2); break;
+    GP_OP_CASE(OP_FWD)
+    GP_OP_CASE(OP_INV)
+    GP_OP_CASE(OP_N_FWD)
+    GP_OP_CASE(OP_INV_N)
+    GP_OP_CASE(OP_INV_N_FWD)
+    GP_OP_CASE(OP_FWD_K_INV)
+#undef GP_OP_CASE
     default:
       break;
   }

@@ -66,6 +66,7 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void*
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
@@ -78,7 +79,7 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 #ifndef GP_TMA_SWIZZLE
 #define GP_TMA_SWIZZLE 0   // measured slower on GB300 than the [pos][pencil] layout with block-wide exchanges
 #endif
-template <int L> struct TmaStrided {
+template <int L, int NSTAGE = 3> struct TmaStrided {
   static constexpr bool SWZ = GP_TMA_SWIZZLE && L <= 256;
   static constexpr int B = L >= 1024 ? 4 : (L >= 512 ? 8 : 16);
   static constexpr int TP = L / Plan<L>::E;
@@ -88,7 +89,9 @@ template <int L> struct TmaStrided {
   static constexpr int STAGE = ((((TILE > EXCH ? TILE : EXCH) * 8) + 1023) / 1024) * 128;   // elements, 1 KB multiple
   static constexpr int BOX = L > 256 ? 256 : L;            // pencil extent of one box
   static constexpr int NBOX = L / BOX;
-  static constexpr int S = 3;                              // stages
+  // stages: 3 (a load two tiles ahead), or 2 (one tile ahead, less shared memory: one more
+  // CTA per SM)
+  static constexpr int S = NSTAGE;
   static constexpr bool TWS = L <= 256;                    // twiddles in shared memory
   static constexpr int TWF = tw_size<L, false>(), TWI = tw_size<L, true>();
   static constexpr size_t TWB = TWS ? (size_t)(TWF + TWI) * 16 : 0;
@@ -113,9 +116,9 @@ template <int L> struct TmaContig {
 };
 
 // y or z pencils; tile index -> (field, x0, c), c the other coordinate (z for y pencils, y for z)
-template <int L>
-__global__ void __launch_bounds__(TmaStrided<L>::NT) k_tma_strided(const __grid_constant__ TmaSweepArgs a) {
-  using G = TmaStrided<L>;
+template <int L, int NSTAGE>
+__global__ void __launch_bounds__(TmaStrided<L, NSTAGE>::NT) k_tma_strided(const __grid_constant__ TmaSweepArgs a) {
+  using G = TmaStrided<L, NSTAGE>;
   using V = float2;
   constexpr int B = G::B, S = G::S, TILE = G::TILE, STAGE = G::STAGE, TP = G::TP;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -208,7 +211,13 @@ __global__ void __launch_bounds__(TmaStrided<L>::NT) k_tma_strided(const __grid_
     if (tid == 0) {
       issue_store(tile, s);
       bulk_commit();
-      if (it >= 1) {
+      if constexpr (S == 2) {
+        const int nxt = tile + S * gridDim.x;   // this stage's next tile, once its store has left smem
+        if (nxt < total) {
+          bulk_wait_read0();
+          issue_load(nxt, s);
+        }
+      } else if (it >= 1) {
         const int nxt = tile - gridDim.x + S * gridDim.x;   // the tile the previous stage serves next
         if (nxt < total) {
           bulk_wait_read1();                                // the previous stage's store has left smem
@@ -320,7 +329,19 @@ __global__ void __launch_bounds__(TmaContig<L>::NT) k_tma_contig(const __grid_co
 }
 
 template <int L> struct TmaLaunch {
-  static cudaError_t launch(const TmaSweepArgs& a, int ctas_per_sm, cudaStream_t s) {
+  template <int NSTAGE> static cudaError_t strided(const TmaSweepArgs& a, int ctas_per_sm, int sms, cudaStream_t s) {
+    using G = TmaStrided<L, NSTAGE>;
+    static bool attr = false;
+    if (!attr) cudaFuncSetAttribute(k_tma_strided<L, NSTAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    attr = true;
+    const int tiles = ((L / G::B) * L) * a.count;
+    int grid = sms * ctas_per_sm;
+    if (grid > tiles) grid = tiles;
+    k_tma_strided<L, NSTAGE><<<grid, G::NT, G::SMEM, s>>>(a);
+    return cudaGetLastError();
+  }
+  // stages: 3 or 2 (strided sweeps only)
+  static cudaError_t launch(const TmaSweepArgs& a, int ctas_per_sm, int stages, cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -334,14 +355,7 @@ template <int L> struct TmaLaunch {
       if (grid > tiles) grid = tiles;
       k_tma_contig<L><<<grid, G::NT, G::SMEM, s>>>(a);
     } else {
-      using G = TmaStrided<L>;
-      static bool attr = false;
-      if (!attr) cudaFuncSetAttribute(k_tma_strided<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-      attr = true;
-      const int tiles = ((L / G::B) * L) * a.count;
-      int grid = sms * ctas_per_sm;
-      if (grid > tiles) grid = tiles;
-      k_tma_strided<L><<<grid, G::NT, G::SMEM, s>>>(a);
+      return stages == 2 ? strided<2>(a, ctas_per_sm, sms, s) : strided<3>(a, ctas_per_sm, sms, s);
     }
     return cudaGetLastError();
   }

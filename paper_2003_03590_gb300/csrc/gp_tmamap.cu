@@ -4,7 +4,7 @@
 #include <cstring>
 
 #include "gp_internal.h"
-#include "gp_tma.cuh"
+#include "gp_plane.cuh"
 
 namespace gp {
 
@@ -43,12 +43,20 @@ template <int L> static void box_of(int axis, cuuint32_t box[3]) {
 
 template <int L> static bool swizzled(int axis) { return axis != 0 && TmaStrided<L>::SWZ; }
 
-static bool make_map(CUtensorMap* m, void* base, int n, int axis) {
+static bool encode_box(CUtensorMap* m, void* base, int n, const cuuint32_t box[3], bool swz) {
   auto enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)n};
   cuuint64_t strides[2] = {(cuuint64_t)n * 8, (cuuint64_t)n * n * 8};
-  cuuint32_t box[3], estr[3] = {1, 1, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+static bool make_map(CUtensorMap* m, void* base, int n, int axis) {
+  cuuint32_t box[3];
   bool swz = false;
   switch (n) {
 #define GP_CASE(L) case L: box_of<L>(axis, box); swz = swizzled<L>(axis); break;
@@ -56,23 +64,29 @@ static bool make_map(CUtensorMap* m, void* base, int n, int axis) {
 #undef GP_CASE
     default: return false;
   }
-  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
+  return encode_box(m, base, n, box, swz);
 }
 
-template <int L> static int occupancy_ctas(int axis) {
+template <int L> static int occupancy_ctas(int axis, int stages) {
   int nb = 0;
-  if (axis == 0)
+  if (axis == 0) {
+    cudaFuncSetAttribute(k_tma_contig<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaContig<L>::SMEM);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_contig<L>, TmaContig<L>::NT, TmaContig<L>::SMEM);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_strided<L>, TmaStrided<L>::NT, TmaStrided<L>::SMEM);
-  return nb < 1 ? 1 : nb;
+  } else if (stages == 2) {
+    using G = TmaStrided<L, 2>;
+    cudaFuncSetAttribute(k_tma_strided<L, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_strided<L, 2>, G::NT, G::SMEM);
+  } else {
+    using G = TmaStrided<L, 3>;
+    cudaFuncSetAttribute(k_tma_strided<L, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_strided<L, 3>, G::NT, G::SMEM);
+  }
+  return nb;
 }
 
 cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* status, cudaStream_t s,
-                      int ctas_req) {
+                      int ctas_req, int stages) {
+  if (a.axis == 0) stages = 3;
   static TmaSweepArgs t;   // large: keep it off the stack (launches copy it)
   std::memset(&t, 0, sizeof(t));
   t.count = a.count;
@@ -89,17 +103,52 @@ cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* s
   t.scale_inv = a.scale_inv;
   t.status = status;
   switch (n) {
-#define GP_CASE(L)                                                                     \
-  case L: {                                                                            \
-    static int occ[3] = {0, 0, 0};                                                     \
-    if (!occ[a.axis]) {                                                                \
-      if (a.axis == 0) cudaFuncSetAttribute(k_tma_contig<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaContig<L>::SMEM); \
-      else cudaFuncSetAttribute(k_tma_strided<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaStrided<L>::SMEM); \
-      occ[a.axis] = occupancy_ctas<L>(a.axis);                                            \
-    }                                                                                  \
-    if (occ[a.axis] < 1) return cudaErrorInvalidConfiguration;                                   \
-    return tma_sweep_##L(t, ctas_req > 0 && ctas_req < occ[a.axis] ? ctas_req : occ[a.axis], s); \
+#define GP_CASE(L)                                                                      \
+  case L: {                                                                             \
+    static int occ[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};   /* [axis][stages == 2] */   \
+    int& o = occ[a.axis][stages == 2 ? 1 : 0];                                          \
+    if (o < 0) o = occupancy_ctas<L>(a.axis, stages);                                   \
+    if (o < 1) return cudaErrorInvalidConfiguration;                                    \
+    return tma_sweep_##L(t, ctas_req > 0 && ctas_req < o ? ctas_req : o, stages, s);    \
   }
+    GP_TMA_SIZES(GP_CASE)
+#undef GP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+// the fused plane kernel (gp_plane.cuh): forward y, forward x + K + inverse x, inverse y of
+// every z-plane of the fields psi[0..count) in one launch
+cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* sync, int* status, cudaStream_t s) {
+  static TmaPlaneArgs t;   // large: keep it off the stack (launches copy it)
+  std::memset(&t, 0, sizeof(t));
+  t.count = a.count;
+  cuuint32_t by[3], bx[3];
+  switch (n) {
+#define GP_CASE(L)                                                                          \
+  case L:                                                                                   \
+    by[0] = TmaPlane<L>::B; by[1] = TmaPlane<L>::BOX; by[2] = 1;                            \
+    bx[0] = TmaPlane<L>::BOX; bx[1] = TmaPlane<L>::B; bx[2] = 1;                            \
+    break;
+    GP_TMA_SIZES(GP_CASE)
+#undef GP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  for (int f = 0; f < a.count; ++f)
+    if (!encode_box(&t.map_y[f], psi[f], n, by, false) || !encode_box(&t.map_x[f], psi[f], n, bx, false))
+      return cudaErrorInvalidValue;
+  t.tw_fwd = a.tw_fwd;
+  t.tw_inv = a.tw_inv;
+  t.ekx = a.ekx;
+  t.ek2 = a.ek2;
+  t.sync = sync;
+  t.status = status;
+  cudaError_t e = cudaMemsetAsync(sync, 0, plane_sync_ints(n, a.count) * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  switch (n) {
+#define GP_CASE(L) case L: return tma_plane_##L(t, s);
     GP_TMA_SIZES(GP_CASE)
 #undef GP_CASE
     default:

@@ -5,7 +5,10 @@
 //   0  TMA-pipelined persistent kernel, as many CTAs per SM as fit
 //   1  the same with one CTA per SM (a larger share of L2 and shared-memory bandwidth each)
 //   2  the non-persistent kernel (one tile per CTA, loads and stores by the threads)
-// and keeps the fastest.  Choices are cached in a small JSON file keyed by the GPU's name.
+//   3  (y and z) the TMA kernel with two shared-memory stages instead of three: one tile of
+//      look-ahead, one more CTA per SM
+// and keeps the fastest; the fused plane kernel (op 7) is timed against the three sweeps it
+// replaces.  Choices are cached in a small JSON file keyed by the GPU's name.
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -15,10 +18,15 @@
 
 namespace gp {
 
-int sweep_variant(gp_plan* p, int n, int axis, int op);
-
 static std::string cache_key(const char* gpu, int n, int axis, int op) {
   return std::string(gpu) + "|" + std::to_string(n) + "|" + std::to_string(axis) + "|" + std::to_string(op);
+}
+
+// candidates per kind: 0-2 everywhere, 3 (two stages) for y and z, only 0 and 2 for the plane kernel
+static bool variant_ok(int axis, int op, int v) {
+  if (op == OP_PLANE) return v == VARIANT_TMA || v == VARIANT_PLAIN;
+  if (v == VARIANT_TMA_2STAGE) return axis != 0;
+  return v >= 0 && v <= 2;
 }
 
 // minimal reader/writer for {"key": int, ...}
@@ -50,8 +58,10 @@ extern "C" gp_status gp_plan_autotune(gp_plan* p, const char* cache_path) {
       std::fclose(f);
     }
   }
-  const int kinds[8][2] = {{2, OP_N_FWD}, {2, OP_INV_N_FWD}, {2, OP_INV_N}, {2, OP_FWD},
-                           {2, OP_INV}, {1, OP_FWD}, {1, OP_INV}, {0, OP_FWD_K_INV}};
+  // the fused plane kernel comes last: it is timed against the three sweeps it replaces, each
+  // with the variant chosen for it just before
+  const int kinds[9][2] = {{2, OP_N_FWD}, {2, OP_INV_N_FWD}, {2, OP_INV_N}, {2, OP_FWD}, {2, OP_INV},
+                           {1, OP_FWD},   {1, OP_INV},       {0, OP_FWD_K_INV}, {1, OP_PLANE}};
   std::vector<int> done;
   std::string out_entries;
   for (size_t fi = 0; fi < p->f.size(); ++fi) {
@@ -70,7 +80,7 @@ extern "C" gp_status gp_plan_autotune(gp_plan* p, const char* cache_path) {
       const int axis = kind[0], op = kind[1];
       const long long key = (long long)F.n * 64 + axis * 8 + op;
       int best = -1;
-      if (!cache_lookup(text, cache_key(prop.name, F.n, axis, op), &best) || best < 0 || best > 2) {
+      if (!cache_lookup(text, cache_key(prop.name, F.n, axis, op), &best) || !variant_ok(axis, op, best)) {
         best = 0;
         if (!scratch) {
           GP_CUDA(p, cudaMalloc(&scratch, (size_t)F.npts * 8));
@@ -91,12 +101,14 @@ extern "C" gp_status gp_plan_autotune(gp_plan* p, const char* cache_path) {
         a.ekx = kt;
         a.ek2 = kt + F.n;
         a.scale_inv = 0;
+        if (op == OP_PLANE) {
+          gp_status st = ensure_plane_sync(p, plane_sync_ints(F.n, 1));
+          if (st != GP_OK) return st;
+        }
         float best_ms = 1e30f;
-        for (int var = 0; var < 3; ++var) {
-          auto run = [&]() -> cudaError_t {
-            if (var == 2) return sweep(F.n, a, p->stream);
-            return tma_sweep(F.n, a, &scratch, p->flag + 1, p->stream, var == 1 ? 1 : 0);
-          };
+        for (int var = 0; var < 4; ++var) {
+          if (!variant_ok(axis, op, var)) continue;
+          auto run = [&]() -> cudaError_t { return launch_sweep_variant(p, F.n, a, &scratch, var, p->stream); };
           for (int w = 0; w < 2; ++w) GP_CUDA(p, run());
           GP_CUDA(p, cudaEventRecord(e0, p->stream));
           for (int r = 0; r < 5; ++r) GP_CUDA(p, run());
@@ -161,4 +173,32 @@ extern "C" gp_status gp_plan_autotune(gp_plan* p, const char* cache_path) {
 extern "C" int gp_plan_sweep_variant(gp_plan* p, int n, int axis, int op) {
   if (!p) return -1;
   return sweep_variant(p, n, axis, op);
+}
+
+extern "C" gp_status gp_plan_set_sweep_variant(gp_plan* p, int n, int axis, int op, int variant) {
+  if (!p) return GP_ERR_INVALID_ARG;
+  const bool kind_ok = (axis == 2 && op >= OP_FWD && op <= OP_INV_N) || (axis == 1 && (op == OP_FWD || op == OP_INV)) ||
+                       (axis == 0 && op == OP_FWD_K_INV) || (axis == 1 && op == OP_PLANE);
+  if (!kind_ok || !variant_ok(axis, op, variant))
+    return fail(p, GP_ERR_INVALID_ARG, "gp_plan_set_sweep_variant: unknown sweep kind or variant");
+  if (p->stream) GP_CUDA(p, cudaStreamSynchronize(p->stream));
+  const long long key = (long long)n * 64 + axis * 8 + op;
+  bool found = false;
+  for (auto& e : p->tune)
+    if (e.first == key) {
+      e.second = variant;
+      found = true;
+    }
+  if (!found) p->tune.push_back({key, variant});
+  if (p->cycle_graph) {
+    cudaGraphExecDestroy(p->cycle_graph);
+    p->cycle_graph = nullptr;
+  }
+  if (p->run_graph) {
+    cudaGraphExecDestroy(p->run_graph);
+    p->run_graph = nullptr;
+  }
+  p->run_key.clear();
+  p->last_key.clear();
+  return GP_OK;
 }

@@ -12,7 +12,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (DIAG_NAMES, GP_FP32, GP_FP64, GP_SPLIT_KNK, GP_SPLIT_NKN, SUPPORTED_N, Diag, FieldParams,
+from ._lib import (DIAG_NAMES, GP_FP32, GP_FP64, GP_SPLIT_KNK, GP_SPLIT_NKN, OP_PLANE, SUPPORTED_N, VARIANT_PLAIN,
+                   VARIANT_TMA, VARIANT_TMA_2STAGE, VARIANT_TMA_ONE, Diag, FieldParams,
                    GPError)
 
 
@@ -171,6 +172,17 @@ class Plan:
 
     def sweep_variant(self, n, axis, op):
         return self._lib.gp_plan_sweep_variant(self._h, n, axis, op)
+
+    def sync(self):
+        """Wait for the plan's stream; raises GPError(GP_ERR_TIMEOUT) if a sweep kernel gave up a
+        bounded wait since the last check."""
+        self._check(self._lib.gp_plan_sync(self._h))
+        return self
+
+    def set_sweep_variant(self, n, axis, op, variant):
+        """Choose the kernel of one sweep kind by hand (see gp.h); returns self."""
+        self._check(self._lib.gp_plan_set_sweep_variant(self._h, n, axis, op, variant))
+        return self
 
     def phase_grad(self, field, psi, lam):
         n = self.n(field)

@@ -18,6 +18,7 @@ if not torch.cuda.is_available():
 
 from paper_2003_03590_gb300 import (GP_FP32, GP_FP64, GP_SPLIT_KNK, GP_SPLIT_NKN, GPEvolve,  # noqa: E402
                                     IncompressibleKineticEnergy, Plan, field_params)
+from paper_2003_03590_gb300.gpqt import OP_PLANE, VARIANT_PLAIN, VARIANT_TMA, VARIANT_TMA_2STAGE  # noqa: E402
 
 
 def _op(plan, dt):
@@ -117,6 +118,76 @@ def test_batched_ragged_plan_matches_single_plans_bitwise():
         assert torch.equal(psis[i], singles[i]), i
 
 
+@pytest.mark.parametrize("split", [GP_SPLIT_NKN, GP_SPLIT_KNK])
+def test_fused_plane_kernel_matches_separate_sweeps_bitwise(split):
+    """The fused plane kernel (forward y, x with K, inverse y of every z-plane in one launch,
+    synchronised per plane through global counters) computes exactly what the three separate
+    sweeps compute: same arithmetic, only the schedule differs."""
+    dt = 0.004
+    sizes = [32, 32, 48, 64, 96, 128, 192, 256]
+    fused = Plan([field_params(n, dt, xi_over_dx=1.5, split=split) for n in sizes])
+    sep = Plan([field_params(n, dt, xi_over_dx=1.5, split=split) for n in sizes])
+    for n in set(sizes):
+        assert fused.sweep_variant(n, 1, OP_PLANE) == VARIANT_TMA       # the default
+        sep.set_sweep_variant(n, 1, OP_PLANE, VARIANT_PLAIN)
+    fa = [to_gpu(random_psi(n, 70 + i), np.complex64) for i, n in enumerate(sizes)]
+    fb = [f.clone() for f in fa]
+    fused.step(fa, 5)
+    sep.step(fb, 5)
+    fused.sync()                            # no bounded wait gave up
+    sep.sync()
+    for i, (x, y) in enumerate(zip(fa, fb)):
+        assert torch.equal(x, y), sizes[i]
+    # and repeated (graph-captured cycle of the fused launches)
+    fused.step(fa, 9)
+    sep.step(fb, 9)
+    fused.sync()
+    sep.sync()
+    for i, (x, y) in enumerate(zip(fa, fb)):
+        assert torch.equal(x, y), sizes[i]
+
+
+def test_two_stage_strided_kernels_bitwise():
+    """The y and z TMA kernels with two shared-memory stages (one more CTA per SM) compute what
+    the three-stage kernels compute."""
+    dt = 0.004
+    sizes = [32, 48, 64, 96, 128, 192, 256]
+    ref = Plan([field_params(n, dt, xi_over_dx=1.5) for n in sizes])
+    two = Plan([field_params(n, dt, xi_over_dx=1.5) for n in sizes])
+    for n in sizes:
+        for p in (ref, two):
+            p.set_sweep_variant(n, 1, OP_PLANE, VARIANT_PLAIN)   # y sweeps as separate launches
+        for axis, op in ((2, 3), (2, 4), (2, 5), (1, 1), (1, 2)):
+            two.set_sweep_variant(n, axis, op, VARIANT_TMA_2STAGE)
+    fa = [to_gpu(random_psi(n, 90 + i), np.complex64) for i, n in enumerate(sizes)]
+    fb = [f.clone() for f in fa]
+    ref.step(fa, 5)
+    two.step(fb, 5)
+    ref.sync()
+    two.sync()
+    for i, (x, y) in enumerate(zip(fa, fb)):
+        assert torch.equal(x, y), sizes[i]
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+def test_fused_plane_kernel_large_lengths_bitwise(n):
+    """Lengths above 256: two TMA boxes per pencil, 8 or 4 pencils per tile."""
+    dt = 0.001
+    fused = Plan(field_params(n, dt, xi_over_dx=1.5))
+    sep = Plan(field_params(n, dt, xi_over_dx=1.5)).set_sweep_variant(n, 1, OP_PLANE, VARIANT_PLAIN)
+    g = torch.Generator(device="cuda").manual_seed(n)
+    re = torch.rand((n, n, n), device="cuda", generator=g, dtype=torch.float32)
+    im = torch.rand((n, n, n), device="cuda", generator=g, dtype=torch.float32)
+    x = torch.complex(re - 0.5, im - 0.5)
+    del re, im
+    y = x.clone()
+    fused.step([x], 2)
+    sep.step([y], 2)
+    fused.sync()
+    sep.sync()
+    assert torch.equal(x, y)
+
+
 def test_host_buffer_step_matches_device_step():
     n = 32
     plan = Plan(field_params(n, 0.004, xi_over_dx=1.5))
@@ -152,7 +223,9 @@ def test_repeated_call_replays_whole_run_graph_bitwise():
     for _ in range(3):                      # calls 2 and 3 of plan a replay the whole-run graph
         l0 = launch_count(a)
         a.step(fa, 7)
-        assert launch_count(a) - l0 == 2 * (4 * 7 + 1)   # two groups (16^3 x2, 24^3), 4 sweeps per step + 1
+        # two groups (16^3 x2, 24^3); lengths without TMA kernels take 4 sweeps per step, + 1
+        per_step = [2 if a.sweep_variant(n, 1, OP_PLANE) == VARIANT_TMA else 4 for n in (16, 24)]
+        assert launch_count(a) - l0 == sum(k * 7 + 1 for k in per_step)
     other = [f.clone() for f in fa]
     for _ in range(3):                      # alternating field sets: never the whole-run graph
         b.step(fb, 7)
@@ -170,8 +243,10 @@ def test_autotune_picks_variants_and_caches(tmp_path):
     text = cache.read_text()
     assert text.count("|") >= 2 * 8 * 3          # 8 sweep kinds per length, 3 separators per key
     for n in sizes:
-        for axis, op in ((2, 3), (1, 1), (1, 2), (0, 6)):
-            assert tuned.sweep_variant(n, axis, op) in (0, 1, 2)
+        for axis, op in ((2, 3), (1, 1), (1, 2)):
+            assert tuned.sweep_variant(n, axis, op) in (0, 1, 2, 3)
+        assert tuned.sweep_variant(n, 0, 6) in (0, 1, 2)
+        assert tuned.sweep_variant(n, 1, OP_PLANE) in (VARIANT_TMA, VARIANT_PLAIN)
     again = Plan([field_params(n, dt, xi_over_dx=1.5) for n in sizes]).autotune(cache)   # from the cache
     for n in sizes:
         assert again.sweep_variant(n, 0, 6) == tuned.sweep_variant(n, 0, 6)
