@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip fp64/cufft/large-size/cpu legs")
     ap.add_argument("--sizes", default="512,1024")
     ap.add_argument("--only-step", action="store_true", help="init, warm-up and the timed steps only (profiling)")
+    ap.add_argument("--only-diag", type=int, default=0, metavar="CALLS",
+                    help="init, then CALLS diagnostics calls of the step workload's field (profiling)")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of kernel choices: read if present (no tuning launches), else written")
     return ap.parse_args()
@@ -354,6 +356,12 @@ def main():
     n, K, W = N_MAIN, args.steps, max(3, args.warmup)
 
     plan = make_plan(gq, n, DT_MAIN, gq.GP_FP32)
+    if args.only_diag:
+        psi = init_rvr(gq, plan, seed=rank)
+        ms_call = diag_leg(gq, plan, psi, n, 0.0, calls=args.only_diag)["ms_per_call"]
+        if rank == 0:
+            print(json.dumps({"diagnostics_ms_per_call": ms_call, "calls": args.only_diag, "n": n}))
+        return 0
     plan.autotune(args.tune_cache)             # kernel choice per sweep kind, before any timing
     psi = init_rvr(gq, plan, seed=rank)
     plan.step([psi], W)                       # warm-up (also captures the step graph)

@@ -174,27 +174,10 @@ __device__ __forceinline__ void sweep_op_body(const SweepArgs<T>& a, int t, int 
   store_pattern<T, L, OUT_INV>(v, t, addr);
 }
 
-template <typename T, int L, int B, class Lay, class GetAddr, bool TILE_IN_SMEM = false, bool WARP_X = false,
-          bool TW_SH = false>
-__device__ __forceinline__ void sweep_body(const SweepArgs<T>& a, int t, int p, cpx<T>* sm, const Lay& lay,
-                                           const GetAddr& addr, int i1, int i2) {
-  switch (a.op) {
-#define GP_OP_CASE(OPV) \
-  case OPV: sweep_op_body<OPV, T, L, B, Lay, GetAddr, TILE_IN_SMEM, WARP_X, TW_SH>(a, t, p, sm, lay, addr, i1, i2); break;
-    GP_OP_CASE(OP_FWD)
-    GP_OP_CASE(OP_INV)
-    GP_OP_CASE(OP_N_FWD)
-    GP_OP_CASE(OP_INV_N)
-    GP_OP_CASE(OP_INV_N_FWD)
-    GP_OP_CASE(OP_FWD_K_INV)
-#undef GP_OP_CASE
-    default:
-      break;
-  }
-}
-
-// y or z pencils: a CTA owns B consecutive x of one (z) or (y) line.
-template <typename T, int L>
+// y or z pencils: a CTA owns B consecutive x of one (z) or (y) line.  One kernel per
+// operation: a kernel holds only the code it runs (smaller than one with every operation
+// behind a run-time switch, which missed in the instruction cache).
+template <typename T, int L, int OP>
 __global__ void __launch_bounds__(strided_batch<T, L>() * (L / Plan<L>::E))
     k_sweep_strided(SweepArgs<T> a) {
   using V = cpx<T>;
@@ -209,11 +192,11 @@ __global__ void __launch_bounds__(strided_batch<T, L>() * (L / Plan<L>::E))
   V* base = a.psi[blockIdx.y] + x0 + p + (long)c * sc;
   auto addr = [&](int pos) { return base + (long)pos * st; };
   LayStrided lay{B};
-  sweep_body<T, L, B>(a, t, p, sm, lay, addr, x0 + p, c);
+  sweep_op_body<OP, T, L, B>(a, t, p, sm, lay, addr, x0 + p, c);
 }
 
 // x rows: a CTA owns B consecutive rows (y, z).
-template <typename T, int L>
+template <typename T, int L, int OP>
 __global__ void __launch_bounds__(contig_batch<T, L>() * (L / Plan<L>::E)) k_sweep_contig(SweepArgs<T> a) {
   using V = cpx<T>;
   constexpr int TP = L / Plan<L>::E;
@@ -225,9 +208,14 @@ __global__ void __launch_bounds__(contig_batch<T, L>() * (L / Plan<L>::E)) k_swe
   V* base = a.psi[blockIdx.y] + row * L;
   auto addr = [&](int pos) { return base + pos; };
   LayContig<L> lay;
-  sweep_body<T, L, B, LayContig<L>, decltype(addr), false, (TP <= 32)>(a, t, p, sm, lay, addr, (int)(row % L),
-                                                                        (int)(row / L));
+  sweep_op_body<OP, T, L, B, LayContig<L>, decltype(addr), false, (TP <= 32)>(a, t, p, sm, lay, addr,
+                                                                              (int)(row % L), (int)(row / L));
 }
+
+// Operations each axis supports: y/z pencils every operation but FWD_K_INV; x rows forward,
+// inverse and forward-K-inverse.  Anything else is an invalid launch.
+#define GP_STRIDED_OPS(X) X(OP_FWD) X(OP_INV) X(OP_N_FWD) X(OP_INV_N) X(OP_INV_N_FWD)
+#define GP_CONTIG_OPS(X) X(OP_FWD) X(OP_INV) X(OP_FWD_K_INV)
 
 template <typename T, int L> struct SweepLaunch {
   static constexpr int TP = L / Plan<L>::E;
@@ -235,23 +223,47 @@ template <typename T, int L> struct SweepLaunch {
   static constexpr int BC = contig_batch<T, L>();
   static size_t smem_strided() { return sizeof(cpx<T>) * (size_t)L * BS; }
   static size_t smem_contig() { return sizeof(cpx<T>) * (size_t)contig_pitch<L>() * BC; }
-  static cudaError_t launch(const SweepArgs<T>& a, cudaStream_t s) {
-    if (a.axis == 0) {
-      size_t sm = smem_contig();
-      static bool attr = false;   // set once, outside any stream capture that follows
-      if (!attr && sm > 48 * 1024) cudaFuncSetAttribute(k_sweep_contig<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
-      long rows = (long)L * L;
-      k_sweep_contig<T, L><<<dim3((unsigned)(rows / BC), (unsigned)a.count), BC * TP, sm, s>>>(a);
-    } else {
-      size_t sm = smem_strided();
-      static bool attr = false;
-      if (!attr && sm > 48 * 1024) cudaFuncSetAttribute(k_sweep_strided<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
-      long tiles = (long)(L / BS) * L;
-      k_sweep_strided<T, L><<<dim3((unsigned)tiles, (unsigned)a.count), BS * TP, sm, s>>>(a);
-    }
+  // the shared-memory limit of every operation's kernel, set together on the first launch of
+  // this length (never inside a stream capture: a step's first sweeps run directly)
+  static void set_attributes() {
+    static bool done = false;
+    if (done) return;
+    const size_t sc = smem_contig(), ss = smem_strided();
+#define GP_ATTR_C(OPV)                                                                                  \
+  if (sc > 48 * 1024) cudaFuncSetAttribute(k_sweep_contig<T, L, OPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+#define GP_ATTR_S(OPV)                                                                                  \
+  if (ss > 48 * 1024) cudaFuncSetAttribute(k_sweep_strided<T, L, OPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    GP_CONTIG_OPS(GP_ATTR_C)
+    GP_STRIDED_OPS(GP_ATTR_S)
+#undef GP_ATTR_C
+#undef GP_ATTR_S
+    done = true;
+  }
+  template <int OP> static cudaError_t contig(const SweepArgs<T>& a, cudaStream_t s) {
+    const size_t sm = smem_contig();
+    set_attributes();
+    const long rows = (long)L * L;
+    k_sweep_contig<T, L, OP><<<dim3((unsigned)(rows / BC), (unsigned)a.count), BC * TP, sm, s>>>(a);
     return cudaGetLastError();
+  }
+  template <int OP> static cudaError_t strided(const SweepArgs<T>& a, cudaStream_t s) {
+    const size_t sm = smem_strided();
+    set_attributes();
+    const long tiles = (long)(L / BS) * L;
+    k_sweep_strided<T, L, OP><<<dim3((unsigned)tiles, (unsigned)a.count), BS * TP, sm, s>>>(a);
+    return cudaGetLastError();
+  }
+  static cudaError_t launch(const SweepArgs<T>& a, cudaStream_t s) {
+#define GP_OP_CASE_C(OPV) \
+  case OPV: return contig<OPV>(a, s);
+#define GP_OP_CASE_S(OPV) \
+  case OPV: return strided<OPV>(a, s);
+    if (a.axis == 0) {
+      switch (a.op) { GP_CONTIG_OPS(GP_OP_CASE_C) default: return cudaErrorInvalidValue; }
+    }
+    switch (a.op) { GP_STRIDED_OPS(GP_OP_CASE_S) default: return cudaErrorInvalidValue; }
+#undef GP_OP_CASE_C
+#undef GP_OP_CASE_S
   }
 };
 

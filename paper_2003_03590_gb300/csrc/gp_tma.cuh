@@ -116,7 +116,7 @@ template <int L> struct TmaContig {
 };
 
 // y or z pencils; tile index -> (field, x0, c), c the other coordinate (z for y pencils, y for z)
-template <int L, int NSTAGE>
+template <int L, int NSTAGE, int OP>
 __global__ void __launch_bounds__(TmaStrided<L, NSTAGE>::NT) k_tma_strided(const __grid_constant__ TmaSweepArgs a) {
   using G = TmaStrided<L, NSTAGE>;
   using V = float2;
@@ -200,11 +200,13 @@ __global__ void __launch_bounds__(TmaStrided<L, NSTAGE>::NT) k_tma_strided(const
     if constexpr (G::SWZ) {
       auto addr = [&](int pos) { return sm + swz128(pos * B + p); };
       LayContig<L> lay;
-      sweep_body<float, L, B, LayContig<L>, decltype(addr), true, true, G::TWS>(sa, t, p, sm, lay, addr, x0 + p, c);
+      sweep_op_body<OP, float, L, B, LayContig<L>, decltype(addr), true, true, G::TWS>(sa, t, p, sm, lay, addr, x0 + p,
+                                                                                      c);
     } else {
       auto addr = [&](int pos) { return sm + pos * B + p; };
       LayStrided lay{B};
-      sweep_body<float, L, B, LayStrided, decltype(addr), true, false, G::TWS>(sa, t, p, sm, lay, addr, x0 + p, c);
+      sweep_op_body<OP, float, L, B, LayStrided, decltype(addr), true, false, G::TWS>(sa, t, p, sm, lay, addr, x0 + p,
+                                                                                     c);
     }
     fence_async_smem();
     __syncthreads();
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(TmaStrided<L, NSTAGE>::NT) k_tma_strided(const
 }
 
 // x rows; tile index -> (field, row0); row = y + N z
-template <int L>
+template <int L, int OP>
 __global__ void __launch_bounds__(TmaContig<L>::NT) k_tma_contig(const __grid_constant__ TmaSweepArgs a) {
   using G = TmaContig<L>;
   using V = float2;
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(TmaContig<L>::NT) k_tma_contig(const __grid_co
     const int f = tile / per_field, row = (tile - f * per_field) * B + p;
     // the TMA tile is [box k][row][x within box]
     auto addr = [&](int pos) { return sm + (pos / G::BOX) * (G::BOX * B) + p * G::BOX + (pos % G::BOX); };
-    sweep_body<float, L, B, LayContig<L>, decltype(addr), true, (TP <= 32), G::TWS>(sa, t, p, sm, lay, addr, row % L,
+    sweep_op_body<OP, float, L, B, LayContig<L>, decltype(addr), true, (TP <= 32), G::TWS>(sa, t, p, sm, lay, addr, row % L,
                                                                                        row / L);
     fence_async_smem();
     __syncthreads();
@@ -328,36 +330,78 @@ __global__ void __launch_bounds__(TmaContig<L>::NT) k_tma_contig(const __grid_co
   }
 }
 
+// Launchers: one kernel per (stages, operation); the grid is the CTAs that fit per SM (or
+// ctas_per_sm if smaller) times the SMs, at most one CTA per tile.
 template <int L> struct TmaLaunch {
-  template <int NSTAGE> static cudaError_t strided(const TmaSweepArgs& a, int ctas_per_sm, int sms, cudaStream_t s) {
+  template <class Kern> static int occupancy(Kern k, int threads, size_t smem) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem);
+    return nb;
+  }
+  static int sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+  }
+  // CTAs per SM of every (kernel, operation), queried together on the first launch of this
+  // length (which is never inside a stream capture: a step's first sweeps run directly)
+  enum { K_S2 = 0, K_S3 = 8, K_C = 16 };
+  static const int* occ_table() {
+    static int t[24] = {};
+    static bool done = false;
+    if (!done) {
+#define GP_OCC_S(OPV)                                                                                       \
+  t[K_S2 + OPV] = occupancy(k_tma_strided<L, 2, OPV>, TmaStrided<L, 2>::NT, TmaStrided<L, 2>::SMEM);           \
+  t[K_S3 + OPV] = occupancy(k_tma_strided<L, 3, OPV>, TmaStrided<L, 3>::NT, TmaStrided<L, 3>::SMEM);
+#define GP_OCC_C(OPV) t[K_C + OPV] = occupancy(k_tma_contig<L, OPV>, TmaContig<L>::NT, TmaContig<L>::SMEM);
+      GP_STRIDED_OPS(GP_OCC_S)
+      GP_CONTIG_OPS(GP_OCC_C)
+#undef GP_OCC_S
+#undef GP_OCC_C
+      done = true;
+    }
+    return t;
+  }
+  template <int NSTAGE, int OP> static cudaError_t strided(const TmaSweepArgs& a, int ctas_per_sm, cudaStream_t s) {
     using G = TmaStrided<L, NSTAGE>;
-    static bool attr = false;
-    if (!attr) cudaFuncSetAttribute(k_tma_strided<L, NSTAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    attr = true;
+    const int occ = occ_table()[(NSTAGE == 2 ? K_S2 : K_S3) + OP];
+    if (occ < 1) return cudaErrorInvalidConfiguration;
     const int tiles = ((L / G::B) * L) * a.count;
-    int grid = sms * ctas_per_sm;
+    int grid = sms() * (ctas_per_sm > 0 && ctas_per_sm < occ ? ctas_per_sm : occ);
     if (grid > tiles) grid = tiles;
-    k_tma_strided<L, NSTAGE><<<grid, G::NT, G::SMEM, s>>>(a);
+    k_tma_strided<L, NSTAGE, OP><<<grid, G::NT, G::SMEM, s>>>(a);
     return cudaGetLastError();
   }
-  // stages: 3 or 2 (strided sweeps only)
-  static cudaError_t launch(const TmaSweepArgs& a, int ctas_per_sm, int stages, cudaStream_t s) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (a.axis == 0) {
-      using G = TmaContig<L>;
-      static bool attr = false;
-      if (!attr) cudaFuncSetAttribute(k_tma_contig<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-      attr = true;
-      const int tiles = (L * L / G::B) * a.count;
-      int grid = sms * ctas_per_sm;
-      if (grid > tiles) grid = tiles;
-      k_tma_contig<L><<<grid, G::NT, G::SMEM, s>>>(a);
-    } else {
-      return stages == 2 ? strided<2>(a, ctas_per_sm, sms, s) : strided<3>(a, ctas_per_sm, sms, s);
-    }
+  template <int OP> static cudaError_t contig(const TmaSweepArgs& a, int ctas_per_sm, cudaStream_t s) {
+    using G = TmaContig<L>;
+    const int occ = occ_table()[K_C + OP];
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int tiles = (L * L / G::B) * a.count;
+    int grid = sms() * (ctas_per_sm > 0 && ctas_per_sm < occ ? ctas_per_sm : occ);
+    if (grid > tiles) grid = tiles;
+    k_tma_contig<L, OP><<<grid, G::NT, G::SMEM, s>>>(a);
     return cudaGetLastError();
+  }
+  // stages: 3 or 2 (y/z sweeps only)
+  static cudaError_t launch(const TmaSweepArgs& a, int ctas_per_sm, int stages, cudaStream_t s) {
+#define GP_OP_CASE_C(OPV) \
+  case OPV: return contig<OPV>(a, ctas_per_sm, s);
+#define GP_OP_CASE_S2(OPV) \
+  case OPV: return strided<2, OPV>(a, ctas_per_sm, s);
+#define GP_OP_CASE_S3(OPV) \
+  case OPV: return strided<3, OPV>(a, ctas_per_sm, s);
+    if (a.axis == 0) {
+      switch (a.op) { GP_CONTIG_OPS(GP_OP_CASE_C) default: return cudaErrorInvalidValue; }
+    }
+    if (stages == 2) {
+      switch (a.op) { GP_STRIDED_OPS(GP_OP_CASE_S2) default: return cudaErrorInvalidValue; }
+    }
+    switch (a.op) { GP_STRIDED_OPS(GP_OP_CASE_S3) default: return cudaErrorInvalidValue; }
+#undef GP_OP_CASE_C
+#undef GP_OP_CASE_S2
+#undef GP_OP_CASE_S3
   }
 };
 

@@ -67,23 +67,6 @@ static bool make_map(CUtensorMap* m, void* base, int n, int axis) {
   return encode_box(m, base, n, box, swz);
 }
 
-template <int L> static int occupancy_ctas(int axis, int stages) {
-  int nb = 0;
-  if (axis == 0) {
-    cudaFuncSetAttribute(k_tma_contig<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaContig<L>::SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_contig<L>, TmaContig<L>::NT, TmaContig<L>::SMEM);
-  } else if (stages == 2) {
-    using G = TmaStrided<L, 2>;
-    cudaFuncSetAttribute(k_tma_strided<L, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_strided<L, 2>, G::NT, G::SMEM);
-  } else {
-    using G = TmaStrided<L, 3>;
-    cudaFuncSetAttribute(k_tma_strided<L, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_strided<L, 3>, G::NT, G::SMEM);
-  }
-  return nb;
-}
-
 cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* status, cudaStream_t s,
                       int ctas_req, int stages) {
   if (a.axis == 0) stages = 3;
@@ -103,14 +86,7 @@ cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* s
   t.scale_inv = a.scale_inv;
   t.status = status;
   switch (n) {
-#define GP_CASE(L)                                                                      \
-  case L: {                                                                             \
-    static int occ[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};   /* [axis][stages == 2] */   \
-    int& o = occ[a.axis][stages == 2 ? 1 : 0];                                          \
-    if (o < 0) o = occupancy_ctas<L>(a.axis, stages);                                   \
-    if (o < 1) return cudaErrorInvalidConfiguration;                                    \
-    return tma_sweep_##L(t, ctas_req > 0 && ctas_req < o ? ctas_req : o, stages, s);    \
-  }
+#define GP_CASE(L) case L: return tma_sweep_##L(t, ctas_req, stages, s);
     GP_TMA_SIZES(GP_CASE)
 #undef GP_CASE
     default:
