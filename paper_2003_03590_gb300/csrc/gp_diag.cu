@@ -31,8 +31,10 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// block-reduce NA partial sums and add them to acc[0..NA)
-template <int NA> __device__ __forceinline__ void block_add(double (&v)[NA], double* acc) {
+// block-reduce NA partial sums; the block's sums go to part[blockIdx.x * NA + a].  The
+// per-block sums are added up by k_reduce in a fixed order: no float64 atomics on one
+// address (they serialise), and the totals are the same on every call.
+template <int NA> __device__ __forceinline__ void block_store(double (&v)[NA], double* part) {
   __shared__ double red[NA][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -47,8 +49,26 @@ template <int NA> __device__ __forceinline__ void block_add(double (&v)[NA], dou
     for (int a = 0; a < NA; ++a) {
       double s = lane < nw ? red[a][lane] : 0.0;
       s = warp_sum(s);
-      if (lane == 0) atomicAdd(acc + a, s);
+      if (lane == 0) part[blockIdx.x * NA + a] = s;
     }
+  }
+}
+
+// acc[a] = sum over blocks b of part[b * na + a]; one block of 256 threads
+__global__ void k_reduce(const double* __restrict__ part, int nblocks, int na, double* acc) {
+  __shared__ double red[8][8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int a = 0; a < na; ++a) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += part[b * na + a];
+    s = warp_sum(s);
+    if (lane == 0) red[a][w] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < na) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
+    acc[threadIdx.x] = s;
   }
 }
 
@@ -57,51 +77,131 @@ static inline unsigned rgrid(long long n) {
   return (unsigned)(b < 1 ? 1 : (b > 152LL * 16 ? 152LL * 16 : b));
 }
 
-// sum |psi|^2, sum (|psi|^2 - 1)^2; flags non-finite input
-template <typename T> __global__ void k_phys1(const cpx<T>* __restrict__ psi, long long npts, double* acc, int* flag) {
-  double v[2] = {0.0, 0.0};
-  bool bad = false;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
-    cpx<T> a = psi[i];
-    double r = (double)a.x * a.x + (double)a.y * a.y;
-    bad |= !isfinite(r);
-    v[0] += r;
-    v[1] += (r - 1.0) * (r - 1.0);
+// Sums of NA per-point terms.  float fields: each term is formed in float32 and added to a
+// float32 partial that is moved into a float64 sum every 32 points (a partial of at most 32
+// terms carries a relative rounding of at most 32 * 2^-24, and nearly all of the float64 rate,
+// which this GPU has little of, is avoided); float64 fields: float64 throughout.
+template <typename T, int NA> struct Sums {
+  double d[NA] = {};
+  T f[NA] = {};
+  int k = 0;
+  __device__ __forceinline__ void add(const T (&v)[NA]) {
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int a = 0; a < NA; ++a) d[a] += v[a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < NA; ++a) f[a] += v[a];
+      if (++k == 32) flush();
+    }
   }
+  __device__ __forceinline__ void flush() {
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      d[a] += (double)f[a];
+      f[a] = T(0);
+    }
+    k = 0;
+  }
+};
+
+// rho - 1 = a.x^2 + a.y^2 - 1 to about one rounding of the result, in the field's precision:
+// rounding rho first would leave an absolute error of one ulp of 1 in rho - 1, a large relative
+// one for a nearly uniform density.  float: the two squares split into value + exact error
+// (fma), their sum by Knuth's two-sum, then 1 subtracted from the sum (exact for rho in
+// [1/2, 2], Sterbenz) and the three error terms added.  (float64 arithmetic would do the same
+// but runs at a small fraction of the float32 rate on this GPU.)
+template <typename T> __device__ __forceinline__ T rho_minus_one(cpx<T> a, T* rho) {
+  if constexpr (sizeof(T) == 8) {
+    *rho = a.x * a.x + a.y * a.y;
+    return *rho - 1.0;
+  } else {
+    const float px = a.x * a.x, ex = fmaf(a.x, a.x, -px);
+    const float py = a.y * a.y, ey = fmaf(a.y, a.y, -py);
+    const float s = px + py, bp = s - px, es = (px - (s - bp)) + (py - bp);
+    *rho = s;
+    return (s - 1.0f) + (es + (ex + ey));
+  }
+}
+
+// |psi|^2 below this is treated as zero (1e-12; for float the smallest float not below 1e-12,
+// so that the float comparison agrees with the float64 one)
+template <typename T> __device__ __forceinline__ T eps_rho() {
+  if constexpr (sizeof(T) == 8) return EPS_RHO;
+  else return __int_as_float(0x2b8cbccd);
+}
+
+// grid coordinates of linear index i (fits in 32 bits: N <= 1024)
+__device__ __forceinline__ void coords3(unsigned i, unsigned n, int& ix, int& iy, int& iz) {
+  const unsigned r = i / n;
+  ix = (int)(i - r * n);
+  iz = (int)(r / n);
+  iy = (int)(r - (unsigned)iz * n);
+}
+
+// sum |psi|^2, sum (|psi|^2 - 1)^2; flags non-finite input
+template <typename T> __global__ void k_phys1(const cpx<T>* __restrict__ psi, long long npts, double* part, int* flag) {
+  Sums<T, 2> S;
+  bool bad = false;
+  auto term = [&](cpx<T> a) {
+    T r;
+    const T dm = rho_minus_one(a, &r);
+    bad |= !isfinite(dm);
+    const T v[2] = {r, dm * dm};
+    S.add(v);
+  };
+  // four independent loads per thread in flight: little arithmetic per byte, so a single load
+  // at a time would leave the kernel bound by memory latency
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < npts; i += 4 * stride) {
+    const cpx<T> a0 = psi[i], a1 = psi[i + stride], a2 = psi[i + 2 * stride], a3 = psi[i + 3 * stride];
+    term(a0);
+    term(a1);
+    term(a2);
+    term(a3);
+  }
+  for (; i < npts; i += stride) term(psi[i]);
+  S.flush();
   if (bad) atomicOr(flag, 1);
-  block_add<2>(v, acc);
+  block_store<2>(S.d, part);
 }
 
 // sum |k|^2 |psi_k|^2 (true |k|, Nyquist kept); W_j = i k~_j psi_k
 template <typename T>
-__global__ void k_kspace1(const cpx<T>* __restrict__ ph, cpx<T>* w1, cpx<T>* w2, cpx<T>* w3, int n, double* acc) {
+__global__ void k_kspace1(const cpx<T>* __restrict__ ph, cpx<T>* w1, cpx<T>* w2, cpx<T>* w3, int n, double* part) {
   const long long npts = (long long)n * n * n;
-  double v[1] = {0.0};
+  Sums<T, 1> S;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
-    const double kx = wavenumber(ix, n), ky = wavenumber(iy, n), kz = wavenumber(iz, n);
+    int ix, iy, iz;
+    coords3((unsigned)i, (unsigned)n, ix, iy, iz);
+    const int kx = wavenumber(ix, n), ky = wavenumber(iy, n), kz = wavenumber(iz, n);
     cpx<T> a = ph[i];
-    v[0] += (kx * kx + ky * ky + kz * kz) * ((double)a.x * a.x + (double)a.y * a.y);
+    const T v[1] = {(T)(kx * kx + ky * ky + kz * kz) * (a.x * a.x + a.y * a.y)};
+    S.add(v);
     const T dx = (T)wavenumber_d(ix, n), dy = (T)wavenumber_d(iy, n), dz = (T)wavenumber_d(iz, n);
     w1[i] = cpx<T>{-dx * a.y, dx * a.x};
     w2[i] = cpx<T>{-dy * a.y, dy * a.x};
     w3[i] = cpx<T>{-dz * a.y, dz * a.x};
   }
-  block_add<1>(v, acc);
+  S.flush();
+  block_store<1>(S.d, part);
 }
 
 // u_j, q_j packed as W_j = u_j + i q_j; W0 = rho - 1; sums of |u|^2 / 2 and 2 alpha^2 |q|^2
 template <typename T>
 __global__ void k_phys2(const cpx<T>* __restrict__ psi, cpx<T>* w0, cpx<T>* w1, cpx<T>* w2, cpx<T>* w3, long long npts,
-                        double alpha, double* acc) {
-  double v[2] = {0.0, 0.0};
-  const T a2 = (T)(2.0 * alpha);
+                        double alpha, double* part) {
+  Sums<T, 2> S;
+  const T a2 = (T)(2.0 * alpha), qa = (T)(2.0 * alpha * alpha);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
     cpx<T> p = psi[i];
-    const T rho = p.x * p.x + p.y * p.y;
+    T rho;
+    const T dm = rho_minus_one(p, &rho);
     cpx<T>* ws[3] = {w1, w2, w3};
-    const bool ok = (double)rho >= EPS_RHO;
+    const bool ok = rho >= eps_rho<T>();
     const T inv_amp = ok ? T(1) / sqrt(rho) : T(0);
+    T v[2] = {T(0), T(0)};
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       cpx<T> g = ws[j][i];
@@ -109,18 +209,22 @@ __global__ void k_phys2(const cpx<T>* __restrict__ psi, cpx<T>* w0, cpx<T>* w1, 
       const T im = p.x * g.y - p.y * g.x;   // Im(conj(psi) g)
       const T u = a2 * im * inv_amp, q = re * inv_amp;
       ws[j][i] = cpx<T>{u, q};
-      v[0] += 0.5 * (double)u * u;
-      v[1] += 2.0 * alpha * alpha * (double)q * q;
+      v[0] += T(0.5) * u * u;
+      v[1] += qa * q * q;
     }
-    w0[i] = cpx<T>{rho - T(1), T(0)};
+    S.add(v);
+    w0[i] = cpx<T>{dm, T(0)};
   }
-  block_add<2>(v, acc);
+  S.flush();
+  block_store<2>(S.d, part);
 }
 
 // Add v[0..4) to hist[q * nbins + b] for every lane of a warp (b < 0: nothing).  Runs of equal b
 // over consecutive lanes (consecutive kx in a row: the shell changes slowly) are summed with a
-// segmented shuffle scan first, so one atomic per run reaches shared memory instead of one per lane.
-__device__ __forceinline__ void bin_add(double* hist, int nbins, int b, double (&v)[4]) {
+// segmented shuffle scan first (in the terms' precision: a run has at most 32 terms), so one
+// float64 shared-memory atomic per run and quantity reaches the histogram instead of one per lane.
+template <typename S>
+__device__ __forceinline__ void bin_add(double* hist, int nbins, int b, S (&v)[4]) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int bprev = __shfl_up_sync(full, b, 1);
@@ -128,7 +232,7 @@ __device__ __forceinline__ void bin_add(double* hist, int nbins, int b, double (
   const int start = 31 - __clz(heads & ((2u << lane) - 1u));   // first lane of this lane's run
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    double t[4];
+    S t[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) t[q] = __shfl_up_sync(full, v[q], o);
     if (lane - o >= start) {
@@ -139,35 +243,47 @@ __device__ __forceinline__ void bin_add(double* hist, int nbins, int b, double (
   const int bnext = __shfl_down_sync(full, b, 1);
   if ((lane == 31 || bnext != b) && b >= 0) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) atomicAdd(&hist[q * nbins + b], v[q]);
+    for (int q = 0; q < 4; ++q) atomicAdd(&hist[q * nbins + b], (double)v[q]);
   }
+}
+
+// shell index floor(|k| + 1/2) of the integer |k|^2 = K, exactly: the b with (2b-1)^2 <= 4K < (2b+1)^2
+__device__ __forceinline__ int shell_of(int K) {
+  int b = (int)(sqrtf((float)K) + 0.5f);
+  while ((2 * b + 1) * (2 * b + 1) <= 4 * K) ++b;
+  while (b > 0 && (2 * b - 1) * (2 * b - 1) > 4 * K) --b;
+  return b;
 }
 
 // Helmholtz split and shell binning; spec layout [4][nbins]: E_kin^i, E_kin^c, E_q, E_int (unscaled)
 template <typename T>
 __global__ void k_kspace2(const cpx<T>* __restrict__ w0, const cpx<T>* __restrict__ w1, const cpx<T>* __restrict__ w2,
                           const cpx<T>* __restrict__ w3, int n, int nbins, double alpha, double beta, double* spec) {
+  using S = T;   // per-point arithmetic in the field's precision
   extern __shared__ double hist[];
   for (int b = threadIdx.x; b < 4 * nbins; b += blockDim.x) hist[b] = 0.0;
   __syncthreads();
   const long long npts = (long long)n * n * n;
   const cpx<T>* ws[3] = {w1, w2, w3};
   const int lane = threadIdx.x & 31;
+  const S qa = (S)(2.0 * alpha * alpha), ab = (S)(alpha * beta);
   // warp-uniform trip count: lane i of a warp handles base + i
   for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < npts;
        base += (long long)gridDim.x * blockDim.x) {
     const long long i = base + lane;
     int b = -1;
-    double val[4] = {0.0, 0.0, 0.0, 0.0};
-    if (i < npts) {
-      // per-point arithmetic in the field's precision (float64 is slow on this part); the sums that
-      // follow are float64
-      using S = T;
-      const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
-      const int mx = (n - ix) % n, my = (n - iy) % n, mz = (n - iz) % n;
-      const long long im = ((long long)mz * n + my) * n + mx;
+    S val[4] = {S(0), S(0), S(0), S(0)};
+    int ix = 0, iy = 0, iz = 0;
+    if (i < npts) coords3((unsigned)i, (unsigned)n, ix, iy, iz);
+    const int mx = ix ? n - ix : 0, my = iy ? n - iy : 0, mz = iz ? n - iz : 0;
+    const long long im = ((long long)mz * n + my) * n + mx;
+    // The fields u, q, rho - 1 are real, so every quantity at -k equals the one at k (and |-k| =
+    // |k|): the half of k-space with i < im is summed twice, the self-mirrored modes (i = im)
+    // once, and the other half is skipped -- each pair of points is read once.
+    if (i < npts && i <= im) {
+      const S wgt = i < im ? S(2) : S(1);
       const int kx = wavenumber(ix, n), ky = wavenumber(iy, n), kz = wavenumber(iz, n);
-      b = (int)floor(sqrt((double)(kx * kx + ky * ky + kz * kz)) + 0.5);
+      b = shell_of(kx * kx + ky * ky + kz * kz);
       if (b >= nbins) b = nbins - 1;
       const S kd[3] = {(S)wavenumber_d(ix, n), (S)wavenumber_d(iy, n), (S)wavenumber_d(iz, n)};
       S ur[3], ui[3], eq = 0;
@@ -195,11 +311,14 @@ __global__ void k_kspace2(const cpx<T>* __restrict__ w0, const cpx<T>* __restric
         const S uir = ur[j] - ucr, uii = ui[j] - uci;
         ei += uir * uir + uii * uii;
       }
-      cpx<T> r = w0[i];
-      val[0] = 0.5 * (double)ei;
-      val[1] = 0.5 * (double)ec;
-      val[2] = 2.0 * alpha * alpha * (double)eq;
-      val[3] = alpha * beta * ((double)r.x * r.x + (double)r.y * r.y);
+      // u_k and q_k at -k are exactly the conjugates of those at k (same operations on the
+      // same two values), so the pair counts twice; the transform of the real rho - 1 is
+      // conjugate-symmetric only up to rounding, so both of its values are read
+      const cpx<T> r = w0[i], rm = w0[im];
+      val[0] = S(0.5) * wgt * ei;
+      val[1] = S(0.5) * wgt * ec;
+      val[2] = qa * wgt * eq;
+      val[3] = ab * (i < im ? (r.x * r.x + r.y * r.y) + (rm.x * rm.x + rm.y * rm.y) : (r.x * r.x + r.y * r.y));
     }
     bin_add(hist, nbins, b, val);
   }
@@ -216,34 +335,49 @@ static gp_status diag_impl(gp_plan* p, int field, const cpx<T>* psi, gp_diag* ou
   const int nbins = gp_plan_nbins(p, field);
   cudaStream_t s = p->stream;
   const size_t fb = (size_t)npts * sizeof(cpx<T>);
-  gp_status st = ensure_ws(p, field, 4 * fb + (size_t)4 * nbins * sizeof(double));
+  const unsigned g = rgrid(npts);
+  gp_status st = ensure_ws(p, field, 4 * fb + (size_t)4 * nbins * sizeof(double) + (size_t)5 * g * sizeof(double));
   if (st != GP_OK) return st;
   cpx<T>* w0 = (cpx<T>*)F.ws;
   cpx<T>* w1 = w0 + npts;
   cpx<T>* w2 = w1 + npts;
   cpx<T>* w3 = w2 + npts;
   double* spec = (double*)(w3 + npts);
+  double* part = spec + 4 * nbins;   // per-block sums: [g][2] + [g][1] + [g][2]
   GP_CUDA(p, cudaMemsetAsync(p->acc, 0, 8 * sizeof(double), s));
   GP_CUDA(p, cudaMemsetAsync(p->flag, 0, sizeof(int), s));
   GP_CUDA(p, cudaMemsetAsync(spec, 0, (size_t)4 * nbins * sizeof(double), s));
-  k_phys1<T><<<rgrid(npts), 256, 0, s>>>(psi, npts, p->acc, p->flag);
+  k_phys1<T><<<g, 256, 0, s>>>(psi, npts, part, p->flag);
+  GP_CUDA(p, cudaGetLastError());
+  k_reduce<<<1, 256, 0, s>>>(part, (int)g, 2, p->acc);
   GP_CUDA(p, cudaGetLastError());
   GP_CUDA(p, cudaMemcpyAsync(w0, psi, fb, cudaMemcpyDeviceToDevice, s));
-  GP_CUDA(p, fft3<T>(F, w0, false, s));
-  k_kspace1<T><<<rgrid(npts), 256, 0, s>>>(w0, w1, w2, w3, n, p->acc + 2);
+  cpx<T>* all[4] = {w0, w1, w2, w3};
+  // 3D transforms: float32 fields through the tuned sweep kernels, several fields per launch
+  auto transform = [&](int first, int count, bool inverse) -> cudaError_t {
+    if constexpr (sizeof(T) == 4) return fft3_many(p, F, all + first, count, inverse, s);
+    for (int k = first; k < first + count; ++k) {
+      cudaError_t e = fft3<T>(F, all[k], inverse, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  GP_CUDA(p, transform(0, 1, false));
+  k_kspace1<T><<<g, 256, 0, s>>>(w0, w1, w2, w3, n, part + 2 * g);
   GP_CUDA(p, cudaGetLastError());
-  GP_CUDA(p, fft3<T>(F, w1, true, s));
-  GP_CUDA(p, fft3<T>(F, w2, true, s));
-  GP_CUDA(p, fft3<T>(F, w3, true, s));
-  k_phys2<T><<<rgrid(npts), 256, 0, s>>>(psi, w0, w1, w2, w3, npts, F.alpha, p->acc + 3);
+  k_reduce<<<1, 256, 0, s>>>(part + 2 * g, (int)g, 1, p->acc + 2);
   GP_CUDA(p, cudaGetLastError());
-  GP_CUDA(p, fft3<T>(F, w0, false, s));
-  GP_CUDA(p, fft3<T>(F, w1, false, s));
-  GP_CUDA(p, fft3<T>(F, w2, false, s));
-  GP_CUDA(p, fft3<T>(F, w3, false, s));
+  GP_CUDA(p, transform(1, 3, true));
+  k_phys2<T><<<g, 256, 0, s>>>(psi, w0, w1, w2, w3, npts, F.alpha, part + 3 * g);
+  GP_CUDA(p, cudaGetLastError());
+  k_reduce<<<1, 256, 0, s>>>(part + 3 * g, (int)g, 2, p->acc + 3);
+  GP_CUDA(p, cudaGetLastError());
+  GP_CUDA(p, transform(0, 4, false));
   const size_t hsm = (size_t)4 * nbins * sizeof(double);
   if (hsm > 48 * 1024) GP_CUDA(p, cudaFuncSetAttribute(k_kspace2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
-  k_kspace2<T><<<rgrid(npts), 256, hsm, s>>>(w0, w1, w2, w3, n, nbins, F.alpha, F.beta, spec);
+  // fewer blocks than the other kernels: each block adds its whole histogram to spec at the end
+  const unsigned g2 = g < 4 * 152 ? g : 4 * 152;
+  k_kspace2<T><<<g2, 256, hsm, s>>>(w0, w1, w2, w3, n, nbins, F.alpha, F.beta, spec);
   GP_CUDA(p, cudaGetLastError());
   double acc[8];
   int flag = 0;
@@ -303,7 +437,8 @@ extern "C" gp_status gp_diagnostics(gp_plan* p, int field, const void* psi, gp_d
 // it uses is a file-scope __device__ array below, reserved when the library is loaded and
 // kept by every GPU that loads it until the process exits:
 //   4 work fields of 64^3 complex64 (8 MiB), the float32 twiddle tables of the supported
-//   lengths up to 64, reduction accumulators, a status word and the shell histogram.
+//   lengths up to 64, reduction accumulators and per-block partial sums, a status word and the
+//   shell histogram.
 // All calls share these arrays, which keep the last call's contents; every call clears the
 // accumulators and histogram it uses.  Calls that overlap on the GPU (two streams, two host
 // threads) race on them: serialise them.
@@ -319,6 +454,8 @@ constexpr int NOALLOC_SIZES[7] = {8, 12, 16, 24, 32, 48, 64};
 static __device__ __align__(256) float2 g_na_work[4 * NOALLOC_MAX_PTS];
 static __device__ __align__(256) float4 g_na_tw[NOALLOC_TW];
 static __device__ __align__(256) double g_na_acc[8];
+constexpr int NOALLOC_MAX_BLOCKS = (int)(NOALLOC_MAX_PTS / 256);   // grid of the pointwise kernels at 64^3
+static __device__ __align__(256) double g_na_part[5 * NOALLOC_MAX_BLOCKS];
 static __device__ __align__(256) double g_na_spec[4 * NOALLOC_MAX_BINS];
 static __device__ __align__(256) int g_na_flag[4];
 
@@ -328,6 +465,7 @@ struct NoAllocDevice {
   float2* work = nullptr;
   float4* tw = nullptr;
   double* acc = nullptr;
+  double* part = nullptr;
   double* spec = nullptr;
   int* flag = nullptr;
   int tw_off[7][2] = {};   // offset of each length's (forward, inverse) table in tw
@@ -361,6 +499,7 @@ static gp_status noalloc_setup(int dev, NoAllocDevice& D) {
   if (cudaGetSymbolAddress((void**)&D.work, g_na_work) != cudaSuccess) return GP_ERR_CUDA;
   if (cudaGetSymbolAddress((void**)&D.tw, g_na_tw) != cudaSuccess) return GP_ERR_CUDA;
   if (cudaGetSymbolAddress((void**)&D.acc, g_na_acc) != cudaSuccess) return GP_ERR_CUDA;
+  if (cudaGetSymbolAddress((void**)&D.part, g_na_part) != cudaSuccess) return GP_ERR_CUDA;
   if (cudaGetSymbolAddress((void**)&D.spec, g_na_spec) != cudaSuccess) return GP_ERR_CUDA;
   if (cudaGetSymbolAddress((void**)&D.flag, g_na_flag) != cudaSuccess) return GP_ERR_CUDA;
   float4 host[NOALLOC_TW];
@@ -417,14 +556,19 @@ extern "C" gp_status gp_diagnostics_noalloc(int n, double alpha, double beta, co
   if (cudaMemsetAsync(D.acc, 0, 8 * sizeof(double), s) != cudaSuccess) return GP_ERR_CUDA;
   if (cudaMemsetAsync(D.flag, 0, sizeof(int), s) != cudaSuccess) return GP_ERR_CUDA;
   if (cudaMemsetAsync(D.spec, 0, (size_t)4 * nb * sizeof(double), s) != cudaSuccess) return GP_ERR_CUDA;
-  k_phys1<float><<<g, 256, 0, s>>>(x, npts, D.acc, D.flag);
+  if ((long long)g > NOALLOC_MAX_BLOCKS) return GP_ERR_UNSUPPORTED_SIZE;
+  double* part = D.part;
+  k_phys1<float><<<g, 256, 0, s>>>(x, npts, part, D.flag);
+  k_reduce<<<1, 256, 0, s>>>(part, (int)g, 2, D.acc);
   if (cudaMemcpyAsync(w0, x, (size_t)npts * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GP_ERR_CUDA;
   if (fft3<float>(F, w0, false, s) != cudaSuccess) return GP_ERR_CUDA;
-  k_kspace1<float><<<g, 256, 0, s>>>(w0, w1, w2, w3, n, D.acc + 2);
+  k_kspace1<float><<<g, 256, 0, s>>>(w0, w1, w2, w3, n, part + 2 * g);
+  k_reduce<<<1, 256, 0, s>>>(part + 2 * g, (int)g, 1, D.acc + 2);
   if (fft3<float>(F, w1, true, s) != cudaSuccess || fft3<float>(F, w2, true, s) != cudaSuccess ||
       fft3<float>(F, w3, true, s) != cudaSuccess)
     return GP_ERR_CUDA;
-  k_phys2<float><<<g, 256, 0, s>>>(x, w0, w1, w2, w3, npts, alpha, D.acc + 3);
+  k_phys2<float><<<g, 256, 0, s>>>(x, w0, w1, w2, w3, npts, alpha, part + 3 * g);
+  k_reduce<<<1, 256, 0, s>>>(part + 3 * g, (int)g, 2, D.acc + 3);
   for (cpx<float>* w : {w0, w1, w2, w3})
     if (fft3<float>(F, w, false, s) != cudaSuccess) return GP_ERR_CUDA;
   k_kspace2<float><<<g, 256, (size_t)4 * nb * sizeof(double), s>>>(w0, w1, w2, w3, n, nb, alpha, beta, D.spec);

@@ -132,6 +132,9 @@ gp_status ensure_plane_sync(gp_plan* p, size_t ints);
 cudaError_t launch_sweep_variant(gp_plan* p, int n, const SweepArgs<float>& a, void* const* psi, int variant,
                                  cudaStream_t s);
 
+// 3D transforms of several float32 fields of one length through the tuned sweep kernels
+cudaError_t fft3_many(gp_plan* p, FieldPlan& F, cpx<float>* const* xs, int count, bool inverse, cudaStream_t s);
+
 // the time step (gp_step.cu): advance one field by nsteps on the plan's stream
 gp_status step_field(gp_plan* p, int field, void* psi, int nsteps);
 

@@ -71,6 +71,27 @@ cudaError_t launch_sweep_variant(gp_plan* p, int n, const SweepArgs<float>& a, v
   return tma_sweep(n, a, psi, p->flag + 1, s, variant == VARIANT_TMA_ONE ? 1 : 0);
 }
 
+// 3D transforms of `count` float32 fields of one plan length, one launch per axis for all of
+// them, through the kernel variants chosen for the forward and inverse y/z sweeps (x: TMA)
+cudaError_t fft3_many(gp_plan* p, FieldPlan& F, cpx<float>* const* xs, int count, bool inverse, cudaStream_t s) {
+  SweepArgs<float> a{};
+  a.count = count;
+  for (int k = 0; k < count; ++k) a.psi[k] = xs[k];
+  a.tw_fwd = (const tw_t<float>*)F.t32.tw_fwd;
+  a.tw_inv = (const tw_t<float>*)F.t32.tw_inv;
+  a.op = inverse ? OP_INV : OP_FWD;
+  a.scale_inv = 1;
+  void* ptrs[GP_MAXB];
+  for (int k = 0; k < count; ++k) ptrs[k] = xs[k];
+  const int order_f[3] = {0, 1, 2}, order_i[3] = {2, 1, 0};
+  for (int i = 0; i < 3; ++i) {
+    a.axis = inverse ? order_i[i] : order_f[i];
+    cudaError_t e = launch_sweep_variant(p, F.n, a, ptrs, sweep_variant(p, F.n, a.axis, a.op), s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 namespace {
 
 struct Group {
