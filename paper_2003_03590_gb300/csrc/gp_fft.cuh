@@ -207,7 +207,7 @@ template <> struct Plan<96>   { static constexpr int NP = 3, E = 24, R0 = 8,  R1
 template <> struct Plan<128>  { static constexpr int NP = 2, E = 16, R0 = 16, R1 = 8,  R2 = 1; };
 template <> struct Plan<192>  { static constexpr int NP = 3, E = 24, R0 = 8,  R1 = 8,  R2 = 3; };
 template <> struct Plan<256>  { static constexpr int NP = 2, E = 16, R0 = 16, R1 = 16, R2 = 1; };
-template <> struct Plan<512>  { static constexpr int NP = 3, E = 8,  R0 = 8,  R1 = 8,  R2 = 8; };
+template <> struct Plan<512>  { static constexpr int NP = 3, E = 16, R0 = 16, R1 = 16, R2 = 2; };
 template <> struct Plan<1024> { static constexpr int NP = 3, E = 16, R0 = 16, R1 = 16, R2 = 4; };
 
 template <int L> __host__ __device__ constexpr int radix_fwd(int i) {
