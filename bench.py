@@ -140,18 +140,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup():
+def dist_setup(backend=None):
+    """Rank/world from the launcher's environment.  One process per GPU: N > 1 runs N
+    replicas of the workload (no data-path collective); the process group only carries the
+    barriers around the timed region and the max over ranks of the timings (nccl on GPUs,
+    gloo for the CPU tests of this host logic)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    backend = backend or "nccl"
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
+    elif backend == "nccl":
         torch.cuda.set_device(0)
     return world, rank, local
+
+
+def _on_gpu():
+    import torch.distributed as dist
+    return dist.is_initialized() and dist.get_backend() == "nccl"
 
 
 def barrier(world):
@@ -159,7 +172,8 @@ def barrier(world):
         import torch
         import torch.distributed as dist
         dist.barrier()
-        torch.cuda.synchronize()
+        if _on_gpu():
+            torch.cuda.synchronize()
 
 
 def max_over_ranks(x, world):
@@ -167,9 +181,15 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _on_gpu() else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(points_per_rank, steps, world, ms_max):
+    """Whole-job N^3*steps/s: every rank advances its own field (weak scaling), timed by the
+    slowest rank."""
+    return points_per_rank * steps * world / (ms_max / 1e3)
 
 
 def tuned_choices(plan, n):
@@ -376,7 +396,7 @@ def main():
     clk = clocks.stop()
     barrier(world)
     ms = max_over_ranks(ms, world)
-    value = n ** 3 * K * world / (ms / 1e3)
+    value = job_throughput(n ** 3, K, world, ms)
     if args.only_step:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "steps": K, "ms_per_step": ms / K}))
