@@ -197,8 +197,9 @@ long long gp_launch_count(const gp_plan* plan);
  * (axis 1).  For every grid length of the plan's float32 fields and every kind of its time step
  * the tuner times the candidates on a scratch field (allocated and freed here) and keeps the
  * fastest: 0 the TMA-pipelined persistent kernel at full occupancy, 1 the same with one CTA per
- * SM, 2 the non-persistent kernel, 3 (y and z only) the TMA kernel with two shared-memory stages;
- * for op 7, 0 = the fused kernel and 2 = the three separate sweeps with their own variants.  cache_path (NULL: none) names a JSON file of earlier
+ * SM, 2 the non-persistent kernel, 3 (y, z and op 7) the TMA kernel with two shared-memory
+ * stages; for op 7, 0 = the fused kernel, 3 = the fused kernel with two stages, 2 = the three
+ * separate sweeps with their own variants.  cache_path (NULL: none) names a JSON file of earlier
  * choices keyed by GPU name, length, axis and op; cached choices are reused without timing and
  * new ones are added.  Synchronises the stream and drops captured graphs.
  * gp_plan_sweep_variant returns the variant in use for a kind (default 0: fused plane kernel
@@ -215,6 +216,15 @@ gp_status gp_plan_set_sweep_variant(gp_plan* plan, int n, int axis, int op, int 
  * GP_ERR_TIMEOUT (the fields written since then are invalid) and the word is cleared.
  * gp_step_host and gp_diagnostics perform the same check. */
 gp_status gp_plan_sync(gp_plan* plan);
+
+/* Test hook of the bounded waits (no counterpart in the paper): the next launch of the fused
+ * plane kernel never hands out its first `tiles` tiles, so the tiles that depend on them wait
+ * for counts that never complete.  Those waits give up after about a second, the launch ends
+ * with the status word set, and the next gp_plan_sync (or gp_step_host, gp_diagnostics)
+ * returns GP_ERR_TIMEOUT; the field is then invalid, the plan and the CUDA context stay
+ * usable.  Applies to one launch (the step must use the fused kernel: a length with TMA
+ * kernels and the default variant); captured graphs are dropped. */
+gp_status gp_plan_test_timeout(gp_plan* plan, int tiles);
 
 /* Message of the last failed call on this plan ("" if none); valid until the next call. */
 const char* gp_last_error(const gp_plan* plan);

@@ -54,6 +54,7 @@ SIGNATURES = {
     "gp_plan_sweep_variant": (_I, [_P, _I, _I, _I]),
     "gp_plan_set_sweep_variant": (_I, [_P, _I, _I, _I, _I]),
     "gp_plan_sync": (_I, [_P]),
+    "gp_plan_test_timeout": (_I, [_P, _I]),
     "gp_profile": (_I, [_P, _I]),
     "gp_profile_read": (_I, [_P, _I, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)]),
     "gp_launch_count": (ctypes.c_longlong, [_P]),

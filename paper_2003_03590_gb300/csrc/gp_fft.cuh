@@ -61,10 +61,12 @@ __device__ __forceinline__ float kmul(float x, KConst k) { return fmaf(x, k.hi, 
 __device__ __forceinline__ double kmul(double x, KConst k) { return x * k.v; }
 
 // a * (c - i s) forward, a * (c + i s) inverse, for constants c = cos(theta), s = sin(theta)
+// (float: every product-sum is an explicit fma, so that the rounding does not depend on how the
+// compiler would contract a*b + c*d in a given kernel -- all kernel variants agree bitwise)
 template <bool INV, typename V> __device__ __forceinline__ V rotk(V a, KConst c, KConst s) {
   if constexpr (sizeof(a.x) == 4) {
-    const float re_lo = a.x * c.lo + (INV ? -a.y * s.lo : a.y * s.lo);
-    const float im_lo = a.y * c.lo + (INV ? a.x * s.lo : -a.x * s.lo);
+    const float re_lo = fmaf(a.x, c.lo, (INV ? -a.y : a.y) * s.lo);
+    const float im_lo = fmaf(a.y, c.lo, (INV ? a.x : -a.x) * s.lo);
     const float re = fmaf(a.x, c.hi, fmaf(INV ? -a.y : a.y, s.hi, re_lo));
     const float im = fmaf(a.y, c.hi, fmaf(INV ? a.x : -a.x, s.hi, im_lo));
     return V{re, im};
@@ -91,8 +93,8 @@ template <> struct TwT<double> { using v = double2; };
 template <typename T> using tw_t = typename TwT<T>::v;
 
 __device__ __forceinline__ float2 twmul(float2 a, float4 w) {   // a * (w.hi + w.lo), one rounding
-  const float re_lo = a.x * w.z - a.y * w.w;
-  const float im_lo = a.x * w.w + a.y * w.z;
+  const float re_lo = fmaf(a.x, w.z, -a.y * w.w);
+  const float im_lo = fmaf(a.x, w.w, a.y * w.z);
   return float2{fmaf(a.x, w.x, fmaf(-a.y, w.y, re_lo)), fmaf(a.x, w.y, fmaf(a.y, w.x, im_lo))};
 }
 __device__ __forceinline__ double2 twmul(double2 a, double2 w) { return cmul(a, w); }
@@ -109,8 +111,8 @@ __device__ __forceinline__ float2 unit_rotate(float2 v, float c, float s) {
   const float t = (big >= 0.5f) ? ((big - 1.0f) + small) : ((pc - 0.5f) + (ps - 0.5f));
   const float h = -0.5f * (t + (ec + es));
   const float dc = c * h, ds = s * h;
-  const float re = fmaf(v.x, c, fmaf(-v.y, s, v.x * dc - v.y * ds));
-  const float im = fmaf(v.x, s, fmaf(v.y, c, v.x * ds + v.y * dc));
+  const float re = fmaf(v.x, c, fmaf(-v.y, s, fmaf(v.x, dc, -v.y * ds)));
+  const float im = fmaf(v.x, s, fmaf(v.y, c, fmaf(v.x, ds, v.y * dc)));
   return float2{re, im};
 }
 __device__ __forceinline__ double2 unit_rotate(double2 v, double c, double s) { return cmul(v, double2{c, s}); }

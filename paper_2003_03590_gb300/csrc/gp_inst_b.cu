@@ -14,43 +14,37 @@ cudaError_t sweep_f64_192(const SweepArgs<double>& a, cudaStream_t s) { return S
 cudaError_t tma_sweep_32(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
   return TmaLaunch<32>::launch(a, ctas, stages, s);
 }
-cudaError_t tma_plane_32(TmaPlaneArgs& a, cudaStream_t s) {
-  a.lag = TmaPlaneLaunch<32>::lag(TmaPlaneLaunch<32>::grid(a.count));
-  return TmaPlaneLaunch<32>::launch(a, s);
+cudaError_t tma_plane_32(TmaPlaneArgs& a, int stages, cudaStream_t s) {
+  return TmaPlaneLaunch<32>::launch(a, stages, s);
 }
 cudaError_t tma_sweep_48(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
   return TmaLaunch<48>::launch(a, ctas, stages, s);
 }
-cudaError_t tma_plane_48(TmaPlaneArgs& a, cudaStream_t s) {
-  a.lag = TmaPlaneLaunch<48>::lag(TmaPlaneLaunch<48>::grid(a.count));
-  return TmaPlaneLaunch<48>::launch(a, s);
+cudaError_t tma_plane_48(TmaPlaneArgs& a, int stages, cudaStream_t s) {
+  return TmaPlaneLaunch<48>::launch(a, stages, s);
 }
 cudaError_t tma_sweep_64(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
   return TmaLaunch<64>::launch(a, ctas, stages, s);
 }
-cudaError_t tma_plane_64(TmaPlaneArgs& a, cudaStream_t s) {
-  a.lag = TmaPlaneLaunch<64>::lag(TmaPlaneLaunch<64>::grid(a.count));
-  return TmaPlaneLaunch<64>::launch(a, s);
+cudaError_t tma_plane_64(TmaPlaneArgs& a, int stages, cudaStream_t s) {
+  return TmaPlaneLaunch<64>::launch(a, stages, s);
 }
 cudaError_t tma_sweep_96(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
   return TmaLaunch<96>::launch(a, ctas, stages, s);
 }
-cudaError_t tma_plane_96(TmaPlaneArgs& a, cudaStream_t s) {
-  a.lag = TmaPlaneLaunch<96>::lag(TmaPlaneLaunch<96>::grid(a.count));
-  return TmaPlaneLaunch<96>::launch(a, s);
+cudaError_t tma_plane_96(TmaPlaneArgs& a, int stages, cudaStream_t s) {
+  return TmaPlaneLaunch<96>::launch(a, stages, s);
 }
 cudaError_t tma_sweep_128(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
   return TmaLaunch<128>::launch(a, ctas, stages, s);
 }
-cudaError_t tma_plane_128(TmaPlaneArgs& a, cudaStream_t s) {
-  a.lag = TmaPlaneLaunch<128>::lag(TmaPlaneLaunch<128>::grid(a.count));
-  return TmaPlaneLaunch<128>::launch(a, s);
+cudaError_t tma_plane_128(TmaPlaneArgs& a, int stages, cudaStream_t s) {
+  return TmaPlaneLaunch<128>::launch(a, stages, s);
 }
 cudaError_t tma_sweep_192(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
   return TmaLaunch<192>::launch(a, ctas, stages, s);
 }
-cudaError_t tma_plane_192(TmaPlaneArgs& a, cudaStream_t s) {
-  a.lag = TmaPlaneLaunch<192>::lag(TmaPlaneLaunch<192>::grid(a.count));
-  return TmaPlaneLaunch<192>::launch(a, s);
+cudaError_t tma_plane_192(TmaPlaneArgs& a, int stages, cudaStream_t s) {
+  return TmaPlaneLaunch<192>::launch(a, stages, s);
 }
 }  // namespace gp

@@ -8,8 +8,7 @@ cudaError_t sweep_f64_512(const SweepArgs<double>& a, cudaStream_t s) { return S
 cudaError_t tma_sweep_512(const TmaSweepArgs& a, int ctas, int stages, cudaStream_t s) {
   return TmaLaunch<512>::launch(a, ctas, stages, s);
 }
-cudaError_t tma_plane_512(TmaPlaneArgs& a, cudaStream_t s) {
-  a.lag = TmaPlaneLaunch<512>::lag(TmaPlaneLaunch<512>::grid(a.count));
-  return TmaPlaneLaunch<512>::launch(a, s);
+cudaError_t tma_plane_512(TmaPlaneArgs& a, int stages, cudaStream_t s) {
+  return TmaPlaneLaunch<512>::launch(a, stages, s);
 }
 }  // namespace gp

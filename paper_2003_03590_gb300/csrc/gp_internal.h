@@ -22,7 +22,7 @@ struct TmaSweepArgs;
 struct TmaPlaneArgs;
 #define GP_DECL_TMA(L)                                                     \
   cudaError_t tma_sweep_##L(const TmaSweepArgs&, int, int, cudaStream_t);   \
-  cudaError_t tma_plane_##L(TmaPlaneArgs&, cudaStream_t);
+  cudaError_t tma_plane_##L(TmaPlaneArgs&, int, cudaStream_t);
 GP_TMA_SIZES(GP_DECL_TMA)
 #undef GP_DECL_TMA
 bool tma_supported(int n);
@@ -32,7 +32,9 @@ cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* s
                       int stages = 3);     // shared-memory stages of the y/z kernels: 3 or 2
 // launch the fused plane kernel (forward y, forward x + K + inverse x, inverse y) for the
 // fields psi[0..count) of length n; sync: device ints, at least plane_sync_ints(n, count)
-cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* sync, int* status, cudaStream_t s);
+cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* sync, int* status, cudaStream_t s,
+                      int stages = 3,    // shared-memory stages: 3, or 2 (twiddles through L1)
+                      int skip = 0);     // leading tickets never handed out (test of the bounded waits)
 inline size_t plane_sync_ints(int n, int count) { return 1 + 2 * (size_t)n * (size_t)count; }
 
 bool supported_n(int n);
@@ -88,6 +90,7 @@ struct gp_plan {
   std::vector<std::pair<long long, int>> tune;   // (n, axis, op) key -> sweep variant (gp_plan_autotune)
   int* plane_sync = nullptr;               // counters of the fused plane kernel
   size_t plane_sync_ints = 0;
+  int plane_skip = 0;                      // gp_plan_test_timeout: tickets the next launch skips
   bool prof = false;                       // per-launch event timing (gp_profile)
   std::vector<cudaEvent_t> ev_pool;        // recorded events, two per profiled launch
   std::vector<int> ev_kind;                // kind index of each profiled launch
@@ -122,8 +125,8 @@ template <typename T> cudaError_t launch_vjp_nonlinear(const cpx<T>* psi_in, cpx
                                                        double shift, cudaStream_t s);
 
 // sweep variants (gp_step.cu): 0 TMA persistent, 1 TMA one CTA per SM, 2 plain, 3 TMA with two
-// stages (y and z only); for OP_PLANE 0 means the fused plane kernel and 2 the three separate
-// sweeps it replaces
+// stages; for OP_PLANE 0 means the fused plane kernel, 3 the same with two stages and 2 the
+// three separate sweeps it replaces
 enum { VARIANT_TMA = 0, VARIANT_TMA_ONE = 1, VARIANT_PLAIN = 2, VARIANT_TMA_2STAGE = 3 };
 int sweep_variant(gp_plan* p, int n, int axis, int op);
 bool plane_on(gp_plan* p, int n);

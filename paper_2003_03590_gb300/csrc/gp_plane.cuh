@@ -50,9 +50,12 @@ struct TmaPlaneArgs {
   int lag;                      // D: planes between consecutive phases of a plane in the order
   int* sync;                    // [0] ticket counter; [1 + 2 u + q] stored tiles of phase q of plane u
   int* status;                  // set to 1 when a bounded wait gives up
+  int skip;                     // tickets never handed out (0; a test of the bounded waits sets it)
 };
 
-template <int L> struct TmaPlane {
+// NS: shared-memory stages, 3, or 2 with the twiddles read through L1 instead of shared memory
+// (one more CTA per SM at 256, registers capped to fit three)
+template <int L, int NS = 3> struct TmaPlane {
   static constexpr int B = TmaStrided<L>::B;               // pencils (columns or rows) per tile
   static constexpr int TP = L / Plan<L>::E;                // threads per pencil
   static constexpr int NC = B * TP;                        // compute threads
@@ -63,9 +66,10 @@ template <int L> struct TmaPlane {
   static constexpr int STAGE = ((STAGE_C > TILE ? STAGE_C : TILE) + 15) / 16 * 16;   // 128-byte multiple
   static constexpr int BOX = L > 256 ? 256 : L;
   static constexpr int NBOX = L / BOX;
-  static constexpr int S = 3;
+  static constexpr int S = NS;
   static constexpr int CHUNK = 2;                          // tickets taken per atomic
-  static constexpr bool TWS = L <= 256;
+  static constexpr bool TWS = L <= 256 && NS == 3;
+  static constexpr int MINB = (NS == 2 && L <= 256) ? 3 : 2;   // CTAs per SM the registers must allow
   static constexpr int TWF = tw_size<L, false>(), TWI = tw_size<L, true>();
   static constexpr size_t TWB = TWS ? (size_t)(TWF + TWI) * 16 : 0;
   static constexpr size_t SMEM = (size_t)S * STAGE * 8 + 96 + 64 + TWB + 128;   // barriers, ring, twiddles, slack
@@ -136,9 +140,10 @@ __device__ __forceinline__ void plane_item(int ticket, int U, int D, int& ph, in
   }
 }
 
-template <int L>
-__global__ void __launch_bounds__(TmaPlane<L>::NT) k_tma_plane(const __grid_constant__ TmaPlaneArgs a) {
-  using G = TmaPlane<L>;
+template <int L, int NS>
+__global__ void __launch_bounds__(TmaPlane<L, NS>::NT, TmaPlane<L, NS>::MINB)
+    k_tma_plane(const __grid_constant__ TmaPlaneArgs a) {
+  using G = TmaPlane<L, NS>;
   using V = float2;
   constexpr int B = G::B, S = G::S, STAGE = G::STAGE, TP = G::TP, Q = G::Q, BOX = G::BOX, NC = G::NC;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(TmaPlane<L>::NT) k_tma_plane(const __grid_cons
       auto claim = [&]() {   // make `pend` the next item in ticket order and start reading its count
         if (pend >= 0 || exhausted) return;
         if (c_next >= c_end) {
-          const int t0 = atomicAdd(a.sync, CHUNK);
+          const int t0 = atomicAdd(a.sync, CHUNK) + a.skip;
           if (t0 >= total) {
             exhausted = true;
             return;
@@ -343,23 +348,23 @@ __global__ void __launch_bounds__(TmaPlane<L>::NT) k_tma_plane(const __grid_cons
 }
 
 template <int L> struct TmaPlaneLaunch {
-  static int occupancy() {
-    static int occ = -1;
+  template <int NS> static int occupancy() {
+    static int occ = -1;   // set on the first launch of the length, before any graph capture
     if (occ < 0) {
-      cudaFuncSetAttribute(k_tma_plane<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaPlane<L>::SMEM);
+      cudaFuncSetAttribute(k_tma_plane<L, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaPlane<L, NS>::SMEM);
       int nb = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_plane<L>, TmaPlane<L>::NT, TmaPlane<L>::SMEM);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_plane<L, NS>, TmaPlane<L, NS>::NT, TmaPlane<L, NS>::SMEM);
       occ = nb;
     }
     return occ;
   }
   // grid for a launch over `count` fields (the lag depends on it)
-  static int grid(int count) {
+  template <int NS> static int grid(int count) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int items = 3 * count * L * TmaPlane<L>::Q;
-    int g = sms * (occupancy() > 0 ? occupancy() : 1);
+    const int items = 3 * count * L * TmaPlane<L, NS>::Q;
+    int g = sms * (occupancy<NS>() > 0 ? occupancy<NS>() : 1);
     return g > items ? items : g;
   }
   // Tickets in flight: each CTA holds up to S loaded items, the rest of a chunk and the item
@@ -367,14 +372,19 @@ template <int L> struct TmaPlaneLaunch {
   // complete by the time it is claimed (measured on GB300 at 256^3: 1x 168 us, 1.5x 154 us,
   // 2x 151 us, 3x 150 us per launch); the data between the phases of a plane (2 lag planes)
   // then still fits in L2.
-  static int lag(int grid) {
-    constexpr int per_plane = 3 * TmaPlane<L>::Q;
-    return (2 * grid * (TmaPlane<L>::S + TmaPlane<L>::CHUNK + 1) + per_plane - 1) / per_plane + 1;
+  template <int NS> static int lag(int grid) {
+    constexpr int per_plane = 3 * TmaPlane<L, NS>::Q;
+    return (2 * grid * (TmaPlane<L, NS>::S + TmaPlane<L, NS>::CHUNK + 1) + per_plane - 1) / per_plane + 1;
   }
-  static cudaError_t launch(const TmaPlaneArgs& a, cudaStream_t s) {
-    if (occupancy() < 1) return cudaErrorInvalidConfiguration;
-    k_tma_plane<L><<<grid(a.count), TmaPlane<L>::NT, TmaPlane<L>::SMEM, s>>>(a);
+  template <int NS> static cudaError_t run(TmaPlaneArgs& a, cudaStream_t s) {
+    if (occupancy<NS>() < 1) return cudaErrorInvalidConfiguration;
+    const int g = grid<NS>(a.count);
+    a.lag = lag<NS>(g);
+    k_tma_plane<L, NS><<<g, TmaPlane<L, NS>::NT, TmaPlane<L, NS>::SMEM, s>>>(a);
     return cudaGetLastError();
+  }
+  static cudaError_t launch(TmaPlaneArgs& a, int stages, cudaStream_t s) {
+    return stages == 2 ? run<2>(a, s) : run<3>(a, s);
   }
 };
 

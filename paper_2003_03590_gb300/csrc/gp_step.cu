@@ -34,7 +34,10 @@ int sweep_variant(gp_plan* p, int n, int axis, int op) {
 }
 
 // forward y, x (forward, K, inverse) and inverse y of a step as one fused plane-kernel launch
-bool plane_on(gp_plan* p, int n) { return sweep_variant(p, n, 1, OP_PLANE) == VARIANT_TMA; }
+bool plane_on(gp_plan* p, int n) {
+  const int v = sweep_variant(p, n, 1, OP_PLANE);
+  return v == VARIANT_TMA || v == VARIANT_TMA_2STAGE;
+}
 
 gp_status ensure_plane_sync(gp_plan* p, size_t ints) {
   if (p->plane_sync_ints >= ints) return GP_OK;
@@ -55,7 +58,11 @@ gp_status ensure_plane_sync(gp_plan* p, size_t ints) {
 cudaError_t launch_sweep_variant(gp_plan* p, int n, const SweepArgs<float>& a, void* const* psi, int variant,
                                  cudaStream_t s) {
   if (a.op == OP_PLANE) {
-    if (variant == VARIANT_TMA) return tma_plane(n, a, psi, p->plane_sync, p->flag + 1, s);
+    if (variant == VARIANT_TMA || variant == VARIANT_TMA_2STAGE) {
+      const int skip = p->plane_skip;
+      p->plane_skip = 0;
+      return tma_plane(n, a, psi, p->plane_sync, p->flag + 1, s, variant == VARIANT_TMA_2STAGE ? 2 : 3, skip);
+    }
     SweepArgs<float> b = a;
     const int ops[3][2] = {{1, OP_FWD}, {0, OP_FWD_K_INV}, {1, OP_INV}};
     for (const auto& o : ops) {

@@ -84,7 +84,9 @@ __device__ __forceinline__ void sincos_m1_small(float x, float* s, float* cm1) {
 // N(s): a * exp(-i coef (|a|^2 - shift)).  For a small phase the product is formed as
 // a + a (cos - 1 - i sin), so its roundings act on the result only and stay unbiased.
 template <typename V, typename S> __device__ __forceinline__ V nonlinear(V a, S coef, S shift) {
-  S r2 = a.x * a.x + a.y * a.y;
+  S r2;
+  if constexpr (sizeof(S) == 4) r2 = fmaf(a.x, a.x, a.y * a.y);   // explicit: see rotk
+  else r2 = a.x * a.x + a.y * a.y;
   S ph = coef * (r2 - shift);
   S sn, cs;
   if constexpr (sizeof(S) == 4) {

@@ -96,7 +96,8 @@ cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* s
 
 // the fused plane kernel (gp_plane.cuh): forward y, forward x + K + inverse x, inverse y of
 // every z-plane of the fields psi[0..count) in one launch
-cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* sync, int* status, cudaStream_t s) {
+cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* sync, int* status, cudaStream_t s,
+                      int stages, int skip) {
   static TmaPlaneArgs t;   // large: keep it off the stack (launches copy it)
   std::memset(&t, 0, sizeof(t));
   t.count = a.count;
@@ -121,10 +122,11 @@ cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* s
   t.ek2 = a.ek2;
   t.sync = sync;
   t.status = status;
+  t.skip = skip;
   cudaError_t e = cudaMemsetAsync(sync, 0, plane_sync_ints(n, a.count) * sizeof(int), s);
   if (e != cudaSuccess) return e;
   switch (n) {
-#define GP_CASE(L) case L: return tma_plane_##L(t, s);
+#define GP_CASE(L) case L: return tma_plane_##L(t, stages, s);
     GP_TMA_SIZES(GP_CASE)
 #undef GP_CASE
     default:

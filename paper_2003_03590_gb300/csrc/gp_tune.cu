@@ -22,9 +22,10 @@ static std::string cache_key(const char* gpu, int n, int axis, int op) {
   return std::string(gpu) + "|" + std::to_string(n) + "|" + std::to_string(axis) + "|" + std::to_string(op);
 }
 
-// candidates per kind: 0-2 everywhere, 3 (two stages) for y and z, only 0 and 2 for the plane kernel
+// candidates per kind: 0-2 everywhere, 3 (two stages) for y, z and the plane kernel; the plane
+// kernel has no one-CTA variant
 static bool variant_ok(int axis, int op, int v) {
-  if (op == OP_PLANE) return v == VARIANT_TMA || v == VARIANT_PLAIN;
+  if (op == OP_PLANE) return v == VARIANT_TMA || v == VARIANT_PLAIN || v == VARIANT_TMA_2STAGE;
   if (v == VARIANT_TMA_2STAGE) return axis != 0;
   return v >= 0 && v <= 2;
 }
@@ -193,6 +194,26 @@ extern "C" gp_status gp_plan_set_sweep_variant(gp_plan* p, int n, int axis, int 
   if (p->cycle_graph) {
     cudaGraphExecDestroy(p->cycle_graph);
     p->cycle_graph = nullptr;
+  }
+  if (p->run_graph) {
+    cudaGraphExecDestroy(p->run_graph);
+    p->run_graph = nullptr;
+  }
+  p->run_key.clear();
+  p->last_key.clear();
+  return GP_OK;
+}
+
+extern "C" gp_status gp_plan_test_timeout(gp_plan* p, int tiles) {
+  if (!p) return GP_ERR_INVALID_ARG;
+  if (tiles < 0) return fail(p, GP_ERR_INVALID_ARG, "gp_plan_test_timeout: negative tile count");
+  if (p->stream) GP_CUDA(p, cudaStreamSynchronize(p->stream));
+  p->plane_skip = tiles;
+  // the setting must reach a direct launch, not a graph captured before it
+  if (p->cycle_graph) {
+    cudaGraphExecDestroy(p->cycle_graph);
+    p->cycle_graph = nullptr;
+    p->cycle_key.clear();
   }
   if (p->run_graph) {
     cudaGraphExecDestroy(p->run_graph);

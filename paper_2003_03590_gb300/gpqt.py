@@ -179,6 +179,12 @@ class Plan:
         self._check(self._lib.gp_plan_sync(self._h))
         return self
 
+    def test_timeout(self, tiles):
+        """Make the next fused-kernel launch skip its first `tiles` tiles (a test of the bounded
+        waits: the launch ends with the status word set; see gp.h)."""
+        self._check(self._lib.gp_plan_test_timeout(self._h, int(tiles)))
+        return self
+
     def set_sweep_variant(self, n, axis, op, variant):
         """Choose the kernel of one sweep kind by hand (see gp.h); returns self."""
         self._check(self._lib.gp_plan_set_sweep_variant(self._h, n, axis, op, variant))

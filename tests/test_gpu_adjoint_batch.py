@@ -126,25 +126,48 @@ def test_fused_plane_kernel_matches_separate_sweeps_bitwise(split):
     dt = 0.004
     sizes = [32, 32, 48, 64, 96, 128, 192, 256]
     fused = Plan([field_params(n, dt, xi_over_dx=1.5, split=split) for n in sizes])
+    two = Plan([field_params(n, dt, xi_over_dx=1.5, split=split) for n in sizes])
     sep = Plan([field_params(n, dt, xi_over_dx=1.5, split=split) for n in sizes])
     for n in set(sizes):
         assert fused.sweep_variant(n, 1, OP_PLANE) == VARIANT_TMA       # the default
+        two.set_sweep_variant(n, 1, OP_PLANE, VARIANT_TMA_2STAGE)      # two stages, twiddles via L1
         sep.set_sweep_variant(n, 1, OP_PLANE, VARIANT_PLAIN)
     fa = [to_gpu(random_psi(n, 70 + i), np.complex64) for i, n in enumerate(sizes)]
     fb = [f.clone() for f in fa]
-    fused.step(fa, 5)
-    sep.step(fb, 5)
-    fused.sync()                            # no bounded wait gave up
-    sep.sync()
-    for i, (x, y) in enumerate(zip(fa, fb)):
-        assert torch.equal(x, y), sizes[i]
-    # and repeated (graph-captured cycle of the fused launches)
-    fused.step(fa, 9)
-    sep.step(fb, 9)
-    fused.sync()
-    sep.sync()
-    for i, (x, y) in enumerate(zip(fa, fb)):
-        assert torch.equal(x, y), sizes[i]
+    fc = [f.clone() for f in fa]
+    for steps in (5, 9):                    # the second call replays the captured cycle
+        fused.step(fa, steps)
+        sep.step(fb, steps)
+        two.step(fc, steps)
+        for p in (fused, sep, two):
+            p.sync()                        # no bounded wait gave up
+        for i, (x, y, z) in enumerate(zip(fa, fb, fc)):
+            assert torch.equal(x, y), sizes[i]
+            assert torch.equal(z, y), sizes[i]
+
+
+def test_bounded_wait_gives_up_and_reports_timeout():
+    """Tiles whose inputs never complete: the fused kernel's waits give up (about a second), the
+    launch ends, the status word reads as GP_ERR_TIMEOUT at the next check, and the plan and the
+    CUDA context stay usable."""
+    from paper_2003_03590_gb300 import GPError
+    n = 32
+    plan = Plan(field_params(n, 0.004, xi_over_dx=1.5))
+    assert plan.sweep_variant(n, 1, OP_PLANE) == VARIANT_TMA
+    psi = to_gpu(random_psi(n, 5), np.complex64)
+    plan.test_timeout(1)                     # the first tile of plane 0 is never processed
+    plan.step([psi], 1)
+    with pytest.raises(GPError) as err:
+        plan.sync()
+    assert err.value.status == 5             # GP_ERR_TIMEOUT
+    # usable afterwards: a clean step on a fresh field, checked against a fresh plan
+    good = to_gpu(random_psi(n, 6), np.complex64)
+    ref = good.clone()
+    plan.step([good], 2)
+    plan.sync()
+    Plan(field_params(n, 0.004, xi_over_dx=1.5)).step([ref], 2)
+    torch.cuda.synchronize()
+    assert torch.equal(good, ref)
 
 
 def test_two_stage_strided_kernels_bitwise():
