@@ -69,7 +69,8 @@ template <int L, int NS = 3> struct TmaPlane {
   static constexpr int S = NS;
   static constexpr int CHUNK = 2;                          // tickets taken per atomic
   static constexpr bool TWS = L <= 256 && NS == 3;
-  static constexpr int MINB = (NS == 2 && L <= 256) ? 3 : 2;   // CTAs per SM the registers must allow
+  // CTAs per SM the registers must allow (shared memory allows one at 1024)
+  static constexpr int MINB = (NS == 2 && L <= 256) ? 3 : (L >= 1024 ? 1 : 2);
   static constexpr int TWF = tw_size<L, false>(), TWI = tw_size<L, true>();
   static constexpr size_t TWB = TWS ? (size_t)(TWF + TWI) * 16 : 0;
   static constexpr size_t SMEM = (size_t)S * STAGE * 8 + 96 + 64 + TWB + 128;   // barriers, ring, twiddles, slack

@@ -81,7 +81,7 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 #endif
 template <int L, int NSTAGE = 3> struct TmaStrided {
   static constexpr bool SWZ = GP_TMA_SWIZZLE && L <= 256;
-  static constexpr int B = L >= 1024 ? 4 : (L >= 512 ? 8 : 16);
+  static constexpr int B = L >= 512 ? 8 : 16;
   static constexpr int TP = L / Plan<L>::E;
   static constexpr int NT = B * TP;
   static constexpr int TILE = B * L;                       // elements
