@@ -210,6 +210,31 @@ gp_status gp_plan_autotune(gp_plan* plan, const char* cache_path);
 int gp_plan_sweep_variant(gp_plan* plan, int n, int axis, int op);
 gp_status gp_plan_set_sweep_variant(gp_plan* plan, int n, int axis, int op, int variant);
 
+/* Imaginary-time preparation (Sec. 4.2) and its start fields (Sec. 5.1, 5.2).
+ * External flows: GP_FLOW_NONE, GP_FLOW_TG (v = (sin x cos y cos z, -cos x sin y cos z, 0)),
+ * GP_FLOW_ABC (the sum of the k = 1 and k = 2 ABC flows with amplitudes abc[0..2] = A, B, C;
+ * abc = NULL: (0.9, 1, 1.1)/sqrt(3)).
+ * gp_init_tg: psi_ARGLE of the Taylor-Green flow (Clebsch potentials, psi_4 to the power
+ *   floor(1/(2 pi alpha)) with the field's alpha and xi = sqrt(alpha/beta)); GP_ERR_INVALID_ARG
+ *   when that power is below 1.  Asynchronous.
+ * gp_init_abc: the ABC start field, a product of phase factors with nearest-integer
+ *   wavenumbers.  Asynchronous.
+ * gp_argle: nsteps >= 0 semi-implicit backward-Euler steps of size dtau > 0 of the advective
+ *   real Ginzburg-Landau flow (eqn:gradient-flow, eqn:semi-backward-Euler) driven by `flow`,
+ *   in place on psi (device, the field's precision).  renorm = 0: the paper's unconstrained
+ *   flow; 1: after every step psi is rescaled to the mean |psi|^2 it had on entry (float64
+ *   sums on the device).  energy_out (NULL: not computed) receives the energy of the driven
+ *   field E_v (eq-energy-num-ext-vel, float64 sums) after the steps; the call then
+ *   synchronises and also reports a sweep kernel's bounded-wait timeout.  Workspace: four
+ *   fields, kept by the plan. */
+#define GP_FLOW_NONE 0
+#define GP_FLOW_TG 1
+#define GP_FLOW_ABC 2
+gp_status gp_init_tg(gp_plan* plan, int field, void* psi_dev);
+gp_status gp_init_abc(gp_plan* plan, int field, void* psi_dev, const double* abc);
+gp_status gp_argle(gp_plan* plan, int field, void* psi_dev, int flow, const double* abc, double dtau, int nsteps,
+                   int renorm, double* energy_out);
+
 /* Waits for the plan's stream and reads the device status word that the persistent sweep
  * kernels set when one of their bounded waits (a TMA copy, a tile counter of the fused plane
  * kernel) gives up instead of hanging.  GP_OK if none did since the last check; otherwise

@@ -34,7 +34,9 @@ ABC (Sec. 5.2): v = v^(1) + v^(2), v^(k) = (B cos ky + C sin kz, C cos kz + A si
 A cos kx + B sin ky), (A, B, C) = (0.9, 1, 1.1)/sqrt(3) by default (ABC); the start field is
 psi^(1) psi^(2), psi^(k) = psi_{A,k}^{x,y,z} psi_{B,k}^{y,z,x} psi_{C,k}^{z,x,y} with
 psi_{A,k}^{x,y,z} = exp(i [A sin(kx)/(2 alpha)] y + i [A cos(kx)/(2 alpha)] z), [a] the nearest
-integer (ABCphi0, ABCphi), the other two by cyclic permutation of (A, x, y, z).
+integer (ABCphi0, ABCphi), the other two by cyclic permutation of (A, x, y, z).  Reading: a
+half-integer [a] rounds away from zero (the paper does not say), with a 1e-9 window so that
+the decision does not depend on the last bit of a.
 """
 import math
 
@@ -120,9 +122,15 @@ def tg_ansatz(n, alpha, beta):
 
 # ---------------- ABC start field ----------------
 
+ROUND_TIE = 1e-9
+
+
 def _round_half_away(a):
-    """Nearest integer, halves away from zero."""
-    return np.sign(a) * np.floor(np.abs(a) + 0.5)
+    """Nearest integer, halves away from zero; a value within 1e-9 of a half counts as the half.
+    (With the default amplitudes and alpha = 0.05, A sin(60 deg) / (2 alpha) is exactly 4.5 and
+    C cos(30 deg) / (2 alpha) exactly 5.5 -- grids whose points include those angles hit the
+    ties, which float64 rounding would otherwise decide either way.)"""
+    return np.sign(a) * np.floor(np.abs(a) + 0.5 + ROUND_TIE)
 
 
 def abc_phase(X, Y, Z, alpha, abc=ABC_DEFAULT):

@@ -12,7 +12,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (DIAG_NAMES, GP_FP32, GP_FP64, GP_SPLIT_KNK, GP_SPLIT_NKN, OP_PLANE, SUPPORTED_N, VARIANT_PLAIN,
+from ._lib import (DIAG_NAMES, GP_FLOW_ABC, GP_FLOW_NONE, GP_FLOW_TG, GP_FP32, GP_FP64, GP_SPLIT_KNK, GP_SPLIT_NKN,
+                   OP_PLANE, SUPPORTED_N, VARIANT_PLAIN,
                    VARIANT_TMA, VARIANT_TMA_2STAGE, VARIANT_TMA_ONE, Diag, FieldParams,
                    GPError)
 
@@ -100,6 +101,33 @@ class Plan:
     def init_rvr(self, field, psi, seed, mode=0, count=40, p0=0.0, p1=0.0):
         self._check(self._lib.gp_init_rvr(self._h, field, _ptr(self._field(psi, field)), seed, mode, count, p0, p1))
         return psi
+
+    # ---- imaginary-time preparation (see gp.h)
+    @staticmethod
+    def _abc_arg(abc):
+        if abc is None:
+            return None, None
+        arr = (ctypes.c_double * 3)(*[float(a) for a in abc])
+        return ctypes.cast(arr, ctypes.c_void_p), arr
+
+    def init_tg(self, field, psi):
+        """Taylor-Green start field psi_ARGLE (Sec. 5.1) into psi."""
+        self._check(self._lib.gp_init_tg(self._h, field, _ptr(self._field(psi, field))))
+        return psi
+
+    def init_abc(self, field, psi, abc=None):
+        """ABC start field (Sec. 5.2); abc = (A, B, C) or None for (0.9, 1, 1.1)/sqrt(3)."""
+        ptr, _keep = self._abc_arg(abc)
+        self._check(self._lib.gp_init_abc(self._h, field, _ptr(self._field(psi, field)), ptr))
+        return psi
+
+    def argle(self, field, psi, flow, dtau, nsteps, abc=None, renorm=False, energy=True):
+        """nsteps imaginary-time (ARGLE) steps in place; returns E_v after them (or None)."""
+        ptr, _keep = self._abc_arg(abc)
+        e = ctypes.c_double()
+        self._check(self._lib.gp_argle(self._h, field, _ptr(self._field(psi, field)), int(flow), ptr, float(dtau),
+                                       int(nsteps), 1 if renorm else 0, ctypes.byref(e) if energy else None))
+        return e.value if energy else None
 
     def psi_from_phase(self, field, theta, out=None):
         if out is None:
