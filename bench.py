@@ -328,6 +328,26 @@ def diag_leg(gq, plan, psi, n, ms_step, calls=3):
     return {"ms_per_call": ms, "share_at_1_per_100_steps": ms / (ms + 100 * ms_step)}
 
 
+def argle_leg(gq, steps=200):
+    """Imaginary-time (ARGLE) preparation of the paper's 128^3 Taylor-Green run (alpha = 0.05,
+    beta = 40, dtau = 1.25e-2): time per ARGLE step (five 3D transforms) in float32 and float64."""
+    import torch
+    out = {}
+    for name, prec in (("f32", gq.GP_FP32), ("f64", gq.GP_FP64)):
+        plan = gq.Plan(gq.field_params(128, 0.001, alpha=0.05, beta=40.0, precision=prec))
+        psi = plan.init_tg(0, plan.empty())
+        plan.argle(0, psi, gq.GP_FLOW_TG, 1.25e-2, 5, energy=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(plan.stream)
+        plan.argle(0, psi, gq.GP_FLOW_TG, 1.25e-2, steps, energy=False)
+        e1.record(plan.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "N3_steps_per_s": 128 ** 3 / (ms / 1e3), "steps": steps}
+    return out
+
+
 def cpu_oracle_baseline(n, dt, steps):
     """The float64 oracle, as it stands, on the host: `steps` full steps of the n^3 workload."""
     from inputs import random_psi
@@ -492,6 +512,7 @@ def main():
         extras["ensemble"] = ensemble_leg(gq)
         extras["adjoint_128"] = adjoint_leg(gq)
         extras["diagnostics_cost"] = diag_leg(gq, plan, psi, n, ms_step)
+        extras["argle_tg_128"] = argle_leg(gq)
         # the float64 oracle on the host cores: one full step of the same 256^3 workload
         val, secs = cpu_oracle_baseline(n, DT_MAIN, 1)
         line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
