@@ -8,6 +8,10 @@ forward DFT F and n = N^3 grid points, Parseval gives mean(|f|^2) =
 sum_k |F f_k|^2 / n^2, which turns the continuous 1/(2 pi)^3 of the spectra
 (Sec. 3.5) into 1/n^2 for mean-normalised energies.
 
+Momentum <rho v> = 2 alpha <Im(psi* grad psi)> (eq-mom-total, eq-scaling-rhov) and the Mach
+numbers of sqrt(rho) v (eq:Mach-Number): M_max = max |sqrt(rho) v| / c, M_rms = sqrt(2 E_kin) / c,
+with the sound speed c = sqrt(2 alpha beta) (c^2 / 2 is the coefficient of (rho - 1)^2 in E).
+
 Readings where the paper is silent (each listed in the design notes):
   * first derivatives use i k~ with the Nyquist component of k~ set to zero;
     the gradient energy in E uses the Laplacian-consistent |k|^2 (Nyquist kept);
@@ -24,7 +28,7 @@ from . import fft
 from .scheme import k2_grid, wavenumbers, wavenumbers_deriv
 
 EPS_RHO = 1e-12
-NAMES = ("N", "E", "E_kin", "E_kin_i", "E_kin_c", "E_q", "E_int")
+NAMES = ("N", "E", "E_kin", "E_kin_i", "E_kin_c", "E_q", "E_int", "P_x", "P_y", "P_z", "M_max", "M_rms")
 SPECTRA = ("E_kin_i", "E_kin_c", "E_q", "E_int")
 
 
@@ -120,6 +124,13 @@ def full(psi, p, with_spectra=True):
         "E_q": float(np.mean(2.0 * p.alpha ** 2 * (q[0] ** 2 + q[1] ** 2 + q[2] ** 2))),
         "E_int": float(np.mean(p.alpha * p.beta * (rho - 1.0) ** 2)),
     }
+    # momentum per unit volume <rho v> = 2 alpha <Im(psi* grad psi)> (eq-mom-total, eq-scaling-rhov)
+    for name, g in zip(("P_x", "P_y", "P_z"), grad):
+        out[name] = 2.0 * p.alpha * float(np.mean(np.imag(np.conj(psi) * g)))
+    # Mach numbers (eq:Mach-Number) of sqrt(rho) v with the sound speed c = sqrt(2 alpha beta)
+    c = math.sqrt(2.0 * p.alpha * p.beta)
+    out["M_max"] = float(np.sqrt(np.max(u[0] ** 2 + u[1] ** 2 + u[2] ** 2))) / c
+    out["M_rms"] = math.sqrt(2.0 * out["E_kin"]) / c
     if not with_spectra:
         return out, None
     nb = nbins(N)

@@ -127,3 +127,37 @@ def test_srp_start_is_vortex_free_once_resolved():
     n = 64
     d, _ = D.full(OI.srp_spectral(n, 1, 2.0), _p(n), with_spectra=False)
     assert d["E_kin_i"] < 1e-12 * d["E_kin_c"]
+
+
+@pytest.mark.parametrize("k,amp", [((1, 0, 0), 1.0), ((2, -1, 3), 0.8)])
+def test_momentum_and_mach_of_a_plane_wave(k, amp):
+    """psi = A exp(i k.x): rho v = 2 alpha |A|^2 k, sqrt(rho) v = 2 alpha |A| k everywhere, so
+    P = 2 alpha A^2 k and M_max = M_rms = 2 alpha A |k| / c with c = sqrt(2 alpha beta)."""
+    n = 16
+    p = S.Params(n=n, alpha=0.3, beta=5.0, dt=0.0)
+    x = 2 * np.pi * np.arange(n) / n
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    psi = amp * np.exp(1j * (k[0] * X + k[1] * Y + k[2] * Z))
+    d, _ = D.full(psi, p, with_spectra=False)
+    for j, name in enumerate(("P_x", "P_y", "P_z")):
+        assert d[name] == pytest.approx(2 * p.alpha * amp ** 2 * k[j], abs=1e-13)
+    m = 2 * p.alpha * amp * math.sqrt(sum(c * c for c in k)) / math.sqrt(2 * p.alpha * p.beta)
+    assert d["M_max"] == pytest.approx(m, rel=1e-12) and d["M_rms"] == pytest.approx(m, rel=1e-12)
+
+
+def test_momentum_by_parseval():
+    """<Im(psi* d_j psi)> = sum_k k~_j |F psi_k|^2 / n^2: the physical-space mean against the
+    spectral sum (numpy's FFT, an independent path)."""
+    n = 12
+    p = S.Params(n=n, alpha=0.2, beta=10.0, dt=0.0)
+    rng = np.random.default_rng(4)
+    psi = rng.normal(size=(n, n, n)) + 1j * rng.normal(size=(n, n, n))
+    d, _ = D.full(psi, p, with_spectra=False)
+    ph = np.fft.fftn(psi)
+    kd = S.wavenumbers_deriv(n)
+    w = np.abs(ph) ** 2 / psi.size ** 2
+    ref = [2 * p.alpha * float(np.sum(kd[None, None, :] * w)), 2 * p.alpha * float(np.sum(kd[None, :, None] * w)),
+           2 * p.alpha * float(np.sum(kd[:, None, None] * w))]
+    for name, r in zip(("P_x", "P_y", "P_z"), ref):
+        assert d[name] == pytest.approx(r, rel=1e-12, abs=1e-14)
+    assert d["M_max"] >= d["M_rms"]
