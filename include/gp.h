@@ -76,6 +76,9 @@ typedef struct {
   double E_kin_c;  /* compressible part */
   double E_q;      /* <2 alpha^2 |grad sqrt(rho)|^2> */
   double E_int;    /* <alpha beta (rho - 1)^2> */
+  double P_x, P_y, P_z;  /* momentum per volume <rho v> = 2 alpha <Im(psi* grad psi)> (eq-mom-total) */
+  double M_max;    /* max |sqrt(rho) v| / c, c = sqrt(2 alpha beta)  (eq:Mach-Number) */
+  double M_rms;    /* sqrt(2 E_kin) / c                              (eq:Mach-Number) */
 } gp_diag;
 
 /* Create a plan for nfields independent fields (a ragged batch is allowed: each

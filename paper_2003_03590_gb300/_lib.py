@@ -23,7 +23,7 @@ class FieldParams(ctypes.Structure):
                 ("split", ctypes.c_int), ("nonlin_minus_one", ctypes.c_int)]
 
 
-DIAG_NAMES = ("N", "E", "E_kin", "E_kin_i", "E_kin_c", "E_q", "E_int")
+DIAG_NAMES = ("N", "E", "E_kin", "E_kin_i", "E_kin_c", "E_q", "E_int", "P_x", "P_y", "P_z", "M_max", "M_rms")
 
 
 class Diag(ctypes.Structure):

@@ -69,28 +69,31 @@ template <typename T> __global__ void k_phys1(const cpx<T>* __restrict__ psi, lo
 template <typename T>
 __global__ void k_kspace1(const cpx<T>* __restrict__ ph, cpx<T>* w1, cpx<T>* w2, cpx<T>* w3, int n, double* part) {
   const long long npts = (long long)n * n * n;
-  Sums<T, 1> S;
+  Sums<T, 4> S;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
     int ix, iy, iz;
     coords3((unsigned)i, (unsigned)n, ix, iy, iz);
     const int kx = wavenumber(ix, n), ky = wavenumber(iy, n), kz = wavenumber(iz, n);
     cpx<T> a = ph[i];
-    const T v[1] = {(T)(kx * kx + ky * ky + kz * kz) * (a.x * a.x + a.y * a.y)};
-    S.add(v);
+    const T a2 = a.x * a.x + a.y * a.y;
     const T dx = (T)wavenumber_d(ix, n), dy = (T)wavenumber_d(iy, n), dz = (T)wavenumber_d(iz, n);
+    // |k|^2 |psi_k|^2 (E's gradient term) and k~_j |psi_k|^2 (the momentum, by Parseval)
+    const T v[4] = {(T)(kx * kx + ky * ky + kz * kz) * a2, dx * a2, dy * a2, dz * a2};
+    S.add(v);
     w1[i] = cpx<T>{-dx * a.y, dx * a.x};
     w2[i] = cpx<T>{-dy * a.y, dy * a.x};
     w3[i] = cpx<T>{-dz * a.y, dz * a.x};
   }
   S.flush();
-  block_store<1>(S.d, part);
+  block_store<4>(S.d, part);
 }
 
 // u_j, q_j packed as W_j = u_j + i q_j; W0 = rho - 1; sums of |u|^2 / 2 and 2 alpha^2 |q|^2
 template <typename T>
 __global__ void k_phys2(const cpx<T>* __restrict__ psi, cpx<T>* w0, cpx<T>* w1, cpx<T>* w2, cpx<T>* w3, long long npts,
-                        double alpha, double* part) {
+                        double alpha, double* part, double* umax) {
   Sums<T, 2> S;
+  T u2max = T(0);   // max |sqrt(rho) v|^2 of this thread (a max is exact in any precision)
   const T a2 = (T)(2.0 * alpha), qa = (T)(2.0 * alpha * alpha);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
     cpx<T> p = psi[i];
@@ -100,6 +103,7 @@ __global__ void k_phys2(const cpx<T>* __restrict__ psi, cpx<T>* w0, cpx<T>* w1, 
     const bool ok = rho >= eps_rho<T>();
     const T inv_amp = ok ? T(1) / sqrt(rho) : T(0);
     T v[2] = {T(0), T(0)};
+    T uu = T(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       cpx<T> g = ws[j][i];
@@ -107,14 +111,27 @@ __global__ void k_phys2(const cpx<T>* __restrict__ psi, cpx<T>* w0, cpx<T>* w1, 
       const T im = p.x * g.y - p.y * g.x;   // Im(conj(psi) g)
       const T u = a2 * im * inv_amp, q = re * inv_amp;
       ws[j][i] = cpx<T>{u, q};
-      v[0] += T(0.5) * u * u;
+      uu += u * u;
       v[1] += qa * q * q;
     }
+    v[0] = T(0.5) * uu;
+    u2max = uu > u2max ? uu : u2max;
     S.add(v);
     w0[i] = cpx<T>{dm, T(0)};
   }
   S.flush();
   block_store<2>(S.d, part);
+  // block max of |u|^2
+  double m = (double)u2max;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double mred[32];
+  if ((threadIdx.x & 31) == 0) mred[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) m = fmax(m, mred[q]);
+    umax[blockIdx.x] = m;
+  }
 }
 
 // Add v[0..4) to hist[q * nbins + b] for every lane of a warp (b < 0: nothing).  Runs of equal b
@@ -225,6 +242,37 @@ __global__ void k_kspace2(const cpx<T>* __restrict__ w0, const cpx<T>* __restric
     if (hist[b] != 0.0) atomicAdd(&spec[b], hist[b]);
 }
 
+// Device accumulators of one diagnostics call:
+//   [0] sum rho  [1] sum (rho-1)^2  [2] sum |k|^2 |psi_k|^2  [3..5] sum k~_j |psi_k|^2
+//   [6] sum |u|^2 / 2  [7] sum 2 alpha^2 |q|^2  [8] max |u|^2
+constexpr int DIAG_ACC = 9;
+
+// The scalars from the accumulators and the shell sums (spectrum q of nb bins at hs + q nb).
+static gp_diag diag_finish(const double* acc, const double* hs, int nb, long long npts, double alpha, double beta) {
+  const double dn = (double)npts, dn2 = dn * dn;
+  gp_diag d{};
+  d.N = acc[0] / dn;
+  d.E_int = alpha * beta * acc[1] / dn;
+  d.E = 2.0 * alpha * alpha * acc[2] / dn2 + d.E_int;
+  // <Im(psi* d_j psi)> = sum_k k~_j |psi_k|^2 / npts^2 (Parseval, unnormalised forward DFT)
+  d.P_x = 2.0 * alpha * acc[3] / dn2;
+  d.P_y = 2.0 * alpha * acc[4] / dn2;
+  d.P_z = 2.0 * alpha * acc[5] / dn2;
+  d.E_kin = acc[6] / dn;
+  d.E_q = acc[7] / dn;
+  double si = 0.0, sc = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    si += hs[b];
+    sc += hs[nb + b];
+  }
+  d.E_kin_i = si / dn2;
+  d.E_kin_c = sc / dn2;
+  const double c = std::sqrt(2.0 * alpha * beta);   // sound speed
+  d.M_max = std::sqrt(acc[8]) / c;
+  d.M_rms = std::sqrt(2.0 * d.E_kin) / c;
+  return d;
+}
+
 template <typename T>
 static gp_status diag_impl(gp_plan* p, int field, const cpx<T>* psi, gp_diag* out, double* spectra, int nbins_req) {
   FieldPlan& F = p->f[field];
@@ -234,15 +282,15 @@ static gp_status diag_impl(gp_plan* p, int field, const cpx<T>* psi, gp_diag* ou
   cudaStream_t s = p->stream;
   const size_t fb = (size_t)npts * sizeof(cpx<T>);
   const unsigned g = rgrid(npts);
-  gp_status st = ensure_ws(p, field, 4 * fb + (size_t)4 * nbins * sizeof(double) + (size_t)5 * g * sizeof(double));
+  gp_status st = ensure_ws(p, field, 4 * fb + (size_t)4 * nbins * sizeof(double) + (size_t)9 * g * sizeof(double));
   if (st != GP_OK) return st;
   cpx<T>* w0 = (cpx<T>*)F.ws;
   cpx<T>* w1 = w0 + npts;
   cpx<T>* w2 = w1 + npts;
   cpx<T>* w3 = w2 + npts;
   double* spec = (double*)(w3 + npts);
-  double* part = spec + 4 * nbins;   // per-block sums: [g][2] + [g][1] + [g][2]
-  GP_CUDA(p, cudaMemsetAsync(p->acc, 0, 8 * sizeof(double), s));
+  double* part = spec + 4 * nbins;   // per-block sums: [g][2] + [g][4] + [g][2] + block maxima [g]
+  GP_CUDA(p, cudaMemsetAsync(p->acc, 0, DIAG_ACC * sizeof(double), s));
   GP_CUDA(p, cudaMemsetAsync(p->flag, 0, sizeof(int), s));
   GP_CUDA(p, cudaMemsetAsync(spec, 0, (size_t)4 * nbins * sizeof(double), s));
   k_phys1<T><<<g, 256, 0, s>>>(psi, npts, part, p->flag);
@@ -263,12 +311,14 @@ static gp_status diag_impl(gp_plan* p, int field, const cpx<T>* psi, gp_diag* ou
   GP_CUDA(p, transform(0, 1, false));
   k_kspace1<T><<<g, 256, 0, s>>>(w0, w1, w2, w3, n, part + 2 * g);
   GP_CUDA(p, cudaGetLastError());
-  k_reduce<<<1, 256, 0, s>>>(part + 2 * g, (int)g, 1, p->acc + 2);
+  k_reduce<<<1, 256, 0, s>>>(part + 2 * g, (int)g, 4, p->acc + 2);
   GP_CUDA(p, cudaGetLastError());
   GP_CUDA(p, transform(1, 3, true));
-  k_phys2<T><<<g, 256, 0, s>>>(psi, w0, w1, w2, w3, npts, F.alpha, part + 3 * g);
+  k_phys2<T><<<g, 256, 0, s>>>(psi, w0, w1, w2, w3, npts, F.alpha, part + 6 * g, part + 8 * g);
   GP_CUDA(p, cudaGetLastError());
-  k_reduce<<<1, 256, 0, s>>>(part + 3 * g, (int)g, 2, p->acc + 3);
+  k_reduce<<<1, 256, 0, s>>>(part + 6 * g, (int)g, 2, p->acc + 6);
+  GP_CUDA(p, cudaGetLastError());
+  k_reduce_max<<<1, 256, 0, s>>>(part + 8 * g, (int)g, p->acc + 8);
   GP_CUDA(p, cudaGetLastError());
   GP_CUDA(p, transform(0, 4, false));
   const size_t hsm = (size_t)4 * nbins * sizeof(double);
@@ -277,10 +327,10 @@ static gp_status diag_impl(gp_plan* p, int field, const cpx<T>* psi, gp_diag* ou
   const unsigned g2 = g < 4 * 152 ? g : 4 * 152;
   k_kspace2<T><<<g2, 256, hsm, s>>>(w0, w1, w2, w3, n, nbins, F.alpha, F.beta, spec);
   GP_CUDA(p, cudaGetLastError());
-  double acc[8];
+  double acc[DIAG_ACC];
   int flag = 0;
   std::vector<double> hs((size_t)4 * nbins);
-  GP_CUDA(p, cudaMemcpyAsync(acc, p->acc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(p, cudaMemcpyAsync(acc, p->acc, sizeof(acc), cudaMemcpyDeviceToHost, s));
   GP_CUDA(p, cudaMemcpyAsync(&flag, p->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   GP_CUDA(p, cudaMemcpyAsync(hs.data(), spec, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
   GP_CUDA(p, cudaStreamSynchronize(s));
@@ -289,22 +339,9 @@ static gp_status diag_impl(gp_plan* p, int field, const cpx<T>* psi, gp_diag* ou
     if (st != GP_OK) return st;
   }
   if (flag) return fail(p, GP_ERR_NONFINITE, "gp_diagnostics: field holds NaN or Inf");
-  const double dn = (double)npts, dn2 = dn * dn;
-  gp_diag d{};
-  d.N = acc[0] / dn;
-  d.E_int = F.alpha * F.beta * acc[1] / dn;
-  d.E = 2.0 * F.alpha * F.alpha * acc[2] / dn2 + d.E_int;
-  d.E_kin = acc[3] / dn;
-  d.E_q = acc[4] / dn;
-  double si = 0.0, sc = 0.0;
-  for (int b = 0; b < nbins; ++b) {
-    si += hs[b];
-    sc += hs[nbins + b];
-  }
-  d.E_kin_i = si / dn2;
-  d.E_kin_c = sc / dn2;
-  *out = d;
+  *out = diag_finish(acc, hs.data(), nbins, npts, F.alpha, F.beta);
   if (spectra) {
+    const double dn2 = (double)npts * (double)npts;
     const int nb = nbins_req < nbins ? nbins_req : nbins;
     for (int q = 0; q < 4; ++q)
       for (int b = 0; b < nb; ++b) spectra[q * nbins_req + b] = hs[(size_t)q * nbins + b] / dn2;
@@ -351,9 +388,9 @@ constexpr int NOALLOC_SIZES[7] = {8, 12, 16, 24, 32, 48, 64};
 
 static __device__ __align__(256) float2 g_na_work[4 * NOALLOC_MAX_PTS];
 static __device__ __align__(256) float4 g_na_tw[NOALLOC_TW];
-static __device__ __align__(256) double g_na_acc[8];
+static __device__ __align__(256) double g_na_acc[DIAG_ACC];
 constexpr int NOALLOC_MAX_BLOCKS = (int)(NOALLOC_MAX_PTS / 256);   // grid of the pointwise kernels at 64^3
-static __device__ __align__(256) double g_na_part[5 * NOALLOC_MAX_BLOCKS];
+static __device__ __align__(256) double g_na_part[9 * NOALLOC_MAX_BLOCKS];
 static __device__ __align__(256) double g_na_spec[4 * NOALLOC_MAX_BINS];
 static __device__ __align__(256) int g_na_flag[4];
 
@@ -451,7 +488,7 @@ extern "C" gp_status gp_diagnostics_noalloc(int n, double alpha, double beta, co
   cpx<float>* w2 = w1 + npts;
   cpx<float>* w3 = w2 + npts;
   const unsigned g = rgrid(npts);
-  if (cudaMemsetAsync(D.acc, 0, 8 * sizeof(double), s) != cudaSuccess) return GP_ERR_CUDA;
+  if (cudaMemsetAsync(D.acc, 0, DIAG_ACC * sizeof(double), s) != cudaSuccess) return GP_ERR_CUDA;
   if (cudaMemsetAsync(D.flag, 0, sizeof(int), s) != cudaSuccess) return GP_ERR_CUDA;
   if (cudaMemsetAsync(D.spec, 0, (size_t)4 * nb * sizeof(double), s) != cudaSuccess) return GP_ERR_CUDA;
   if ((long long)g > NOALLOC_MAX_BLOCKS) return GP_ERR_UNSUPPORTED_SIZE;
@@ -461,17 +498,18 @@ extern "C" gp_status gp_diagnostics_noalloc(int n, double alpha, double beta, co
   if (cudaMemcpyAsync(w0, x, (size_t)npts * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GP_ERR_CUDA;
   if (fft3<float>(F, w0, false, s) != cudaSuccess) return GP_ERR_CUDA;
   k_kspace1<float><<<g, 256, 0, s>>>(w0, w1, w2, w3, n, part + 2 * g);
-  k_reduce<<<1, 256, 0, s>>>(part + 2 * g, (int)g, 1, D.acc + 2);
+  k_reduce<<<1, 256, 0, s>>>(part + 2 * g, (int)g, 4, D.acc + 2);
   if (fft3<float>(F, w1, true, s) != cudaSuccess || fft3<float>(F, w2, true, s) != cudaSuccess ||
       fft3<float>(F, w3, true, s) != cudaSuccess)
     return GP_ERR_CUDA;
-  k_phys2<float><<<g, 256, 0, s>>>(x, w0, w1, w2, w3, npts, alpha, part + 3 * g);
-  k_reduce<<<1, 256, 0, s>>>(part + 3 * g, (int)g, 2, D.acc + 3);
+  k_phys2<float><<<g, 256, 0, s>>>(x, w0, w1, w2, w3, npts, alpha, part + 6 * g, part + 8 * g);
+  k_reduce<<<1, 256, 0, s>>>(part + 6 * g, (int)g, 2, D.acc + 6);
+  k_reduce_max<<<1, 256, 0, s>>>(part + 8 * g, (int)g, D.acc + 8);
   for (cpx<float>* w : {w0, w1, w2, w3})
     if (fft3<float>(F, w, false, s) != cudaSuccess) return GP_ERR_CUDA;
   k_kspace2<float><<<g, 256, (size_t)4 * nb * sizeof(double), s>>>(w0, w1, w2, w3, n, nb, alpha, beta, D.spec);
   if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
-  double acc[8];
+  double acc[DIAG_ACC];
   double hs[4 * NOALLOC_MAX_BINS];
   int flag = 0;
   if (cudaMemcpyAsync(acc, D.acc, sizeof(acc), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -480,21 +518,8 @@ extern "C" gp_status gp_diagnostics_noalloc(int n, double alpha, double beta, co
       cudaStreamSynchronize(s) != cudaSuccess)
     return GP_ERR_CUDA;
   if (flag) return GP_ERR_NONFINITE;
-  const double dn = (double)npts, dn2 = dn * dn;
-  gp_diag d{};
-  d.N = acc[0] / dn;
-  d.E_int = alpha * beta * acc[1] / dn;
-  d.E = 2.0 * alpha * alpha * acc[2] / dn2 + d.E_int;
-  d.E_kin = acc[3] / dn;
-  d.E_q = acc[4] / dn;
-  double si = 0.0, sc = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    si += hs[b];
-    sc += hs[nb + b];
-  }
-  d.E_kin_i = si / dn2;
-  d.E_kin_c = sc / dn2;
-  *out = d;
+  *out = diag_finish(acc, hs, nb, npts, alpha, beta);
+  const double dn2 = (double)npts * (double)npts;
   if (spectra)
     for (int c = 0; c < 4; ++c)
       for (int b = 0; b < nb; ++b) spectra[c * nbins + b] = hs[(size_t)c * nb + b] / dn2;

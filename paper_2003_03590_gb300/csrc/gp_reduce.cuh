@@ -55,6 +55,21 @@ static __global__ void k_reduce(const double* __restrict__ part, int nblocks, in
 }
 
 
+// acc[0] = max over blocks b of part[b] (non-negative values)
+static __global__ void k_reduce_max(const double* __restrict__ part, int nblocks, double* acc) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) m = fmax(m, part[b]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) m = fmax(m, red[q]);
+    *acc = m;
+  }
+}
+
 // target = sum / npts (the mean that a renormalisation keeps)
 static __global__ void k_scale_to_mean(const double* sum, double* target, double npts) { *target = *sum / npts; }
 

@@ -60,6 +60,42 @@ def test_diagnostics_sound_wave_and_srp():
     assert d["E_kin_c"] > 1e6 * max(d["E_kin_i"], 1e-300)
 
 
+@pytest.mark.parametrize("prec", [GP_FP32, GP_FP64])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_momentum_and_mach_of_a_plane_wave(prec, axis):
+    """psi = exp(i m x_j): rho = 1 and v = 2 alpha m e_j everywhere, so P = 2 alpha m e_j,
+    M_max = M_rms = 2 alpha m / sqrt(2 alpha beta) exactly (eq-mom-total, eq:Mach-Number)."""
+    n, m = 32, 3
+    plan = _plan(n, prec)
+    a, b = plan.coefficients()
+    dtype = np.complex128 if prec == GP_FP64 else np.complex64
+    x = 2 * np.pi * np.arange(n) / n
+    grids = np.meshgrid(x, x, x, indexing="ij")       # [z, y, x]
+    coord = grids[2 - axis]
+    d, _ = plan.diagnostics(0, to_gpu(np.exp(1j * m * coord), dtype))
+    tol = 1e-12 if prec == GP_FP64 else 2e-6
+    want = [0.0, 0.0, 0.0]
+    want[axis] = 2 * a * m
+    for j, name in enumerate(("P_x", "P_y", "P_z")):
+        assert abs(d[name] - want[j]) <= tol * 2 * a * m, (name, d[name], want[j])
+    mach = 2 * a * m / math.sqrt(2 * a * b)
+    assert d["M_max"] == pytest.approx(mach, rel=10 * tol)
+    assert d["M_rms"] == pytest.approx(mach, rel=10 * tol)
+
+
+def test_momentum_is_odd_under_conjugation_and_mach_even():
+    """psi -> conj(psi) reverses every velocity: P -> -P, the Mach numbers stay."""
+    n = 32
+    plan = _plan(n, GP_FP64)
+    psi = random_psi(n, 5, amp_jitter=0.25)
+    d, _ = plan.diagnostics(0, to_gpu(psi, np.complex128))
+    c, _ = plan.diagnostics(0, to_gpu(np.conj(psi), np.complex128))
+    for name in ("P_x", "P_y", "P_z"):
+        assert abs(d[name] + c[name]) <= 1e-12 * max(abs(d[name]), 1e-3 * d["E"]), name
+    for name in ("M_max", "M_rms"):
+        assert c[name] == pytest.approx(d[name], rel=1e-12), name
+
+
 def test_diagnostics_rejects_nonfinite():
     n = 16
     plan = _plan(n, GP_FP32)
