@@ -18,6 +18,8 @@ scheme       parameters (Sec. 4.1), sub-flows and Strang steps (Sec. 4.3)
 diagnostics  N, E, hydrodynamic split, Helmholtz split, spectra (Sec. 3.4-3.5, 4.1)
 initial      SRP (Sec. 5.3) and RVR (Sec. 5.4) initial conditions
 adjoint      vector-Jacobian products of the split step (no counterpart in the paper)
+argle        imaginary-time ARGLE step, E_v, Taylor-Green and ABC start fields (Sec. 4.2, 5.1-5.2)
+structure    velocity and longitudinal structure functions (Sec. 3.5)
 
 Pinning: every public function is checked by ``tests/test_oracle_*.py``
 against brute force, closed forms, invariants or library routines; the one
