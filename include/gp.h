@@ -139,6 +139,19 @@ gp_status gp_step_host(gp_plan* plan, void* const* psi_host, int nsteps);
  * Synchronises the plan's stream.  GP_ERR_NONFINITE if psi holds NaN/Inf. */
 gp_status gp_diagnostics(gp_plan* plan, int field, const void* psi, gp_diag* out, double* spectra, int nbins);
 
+/* Longitudinal velocity structure functions (Sec. 3.5, strfunc-def):
+ *   out[j * nr + s] = < (v_j(x + s dx e_j) - v_j(x))^order >,  j = 0 (x), 1 (y), 2 (z),
+ *   s = 0 .. N/2, dx = 2 pi / N (the other shifts follow: S(N dx - r) = (-1)^order S(r)),
+ * a volume mean over the grid, with the superfluid velocity v = 2 alpha Im(psi* grad psi) / |psi|^2
+ * (eq-scaling-rhov; spectral gradient with Nyquist-zeroed wavenumbers; v = 0 where
+ * |psi|^2 < 1e-12).  The paper plots order 2 and checks it against 2 <v_x^2> at large r.
+ *   psi: device field (read only, 16-byte aligned);  order: 1 .. 8;
+ *   out: host array of 3 * nr doubles, nr >= N/2 + 1 (entries beyond N/2 untouched).
+ * Float64 sums; float32 fields form each pencil's sum of N terms in float32.  Uses the plan's
+ * workspace (grown to 4 fields + 1 real field + small sums) and synchronises the plan's stream.
+ * GP_ERR_INVALID_ARG for a bad order, nr or pointer; GP_ERR_NONFINITE if a result is NaN/Inf. */
+gp_status gp_structure_function(gp_plan* plan, int field, const void* psi, int order, double* out, int nr);
+
 /* Adjoint of nsteps split steps (no counterpart in the paper: the transpose of
  * the Sec. 4.3 step under <a, b> = Re sum conj(a) b).
  *   psi_n:  device field, the state at the start of the nsteps steps (read only);

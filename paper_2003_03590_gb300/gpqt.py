@@ -179,6 +179,14 @@ class Plan:
         spec = spec.reshape(4, nb)
         return out, {"E_kin_i": spec[0], "E_kin_c": spec[1], "E_q": spec[2], "E_int": spec[3]}
 
+    def structure_function(self, field, psi, order=2):
+        """S^order along x, y, z at the separations s 2 pi / N, s = 0 .. N/2: array [3, N/2 + 1]."""
+        ns = self.n(field) // 2 + 1
+        out = np.zeros(3 * ns)
+        self._check(self._lib.gp_structure_function(self._h, field, _ptr(self._field(psi, field)), int(order),
+                                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns))
+        return out.reshape(3, ns)
+
     def adjoint_step(self, field, psi_n, lam, nsteps):
         self._check(self._lib.gp_adjoint_step(self._h, field, _ptr(self._field(psi_n, field)),
                                               _ptr(self._field(lam, field)), int(nsteps)))
