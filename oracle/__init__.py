@@ -20,6 +20,7 @@ initial      SRP (Sec. 5.3) and RVR (Sec. 5.4) initial conditions
 adjoint      vector-Jacobian products of the split step (no counterpart in the paper)
 argle        imaginary-time ARGLE step, E_v, Taylor-Green and ABC start fields (Sec. 4.2, 5.1-5.2)
 structure    velocity and longitudinal structure functions (Sec. 3.5)
+helicity     helicity and regularised helicity with their spectra (Sec. 3.6)
 
 Pinning: every public function is checked by ``tests/test_oracle_*.py``
 against brute force, closed forms, invariants or library routines; the one
