@@ -152,6 +152,22 @@ gp_status gp_diagnostics(gp_plan* plan, int field, const void* psi, gp_diag* out
  * GP_ERR_INVALID_ARG for a bad order, nr or pointer; GP_ERR_NONFINITE if a result is NaN/Inf. */
 gp_status gp_structure_function(gp_plan* plan, int field, const void* psi, int order, double* out, int nr);
 
+/* Helicity and regularised helicity (Sec. 3.6: eq-helicity, Hreg), volume means, with
+ * hbar/m = 2 alpha:
+ *   H     = < v . omega >, omega = curl v, v = 2 alpha Im(psi* grad psi) / |psi|^2
+ *           (0 where |psi|^2 < 1e-12; Nyquist-zeroed first derivatives);
+ *   w     = (2 alpha / i) grad psi* x grad psi,
+ *   v_par = 2 alpha w_i Im(sum_j (d_i d_j psi) conj(d_j psi)) / (|w| |grad psi|^2),
+ *   v_reg = v_par w / |w|  (0 where |w| <= 1e-5 * 4 alpha <|grad psi|^2>),
+ *   H_reg = < v_reg . omega >,
+ * second derivatives -k~_i k~_j F psi.  spectra: NULL or 2 * nbins doubles (nbins >=
+ * gp_plan_nbins): [0][b] H(k), [1][b] H_reg(k), the shell sums (b = floor(|k| + 1/2)) of
+ * Re(conj(F v) . F omega) / n^2 and Re(conj(F v_reg) . F omega) / n^2 (H is the sum of its
+ * spectrum).  psi: device field (read only, 16-byte aligned); H, H_reg: host doubles.
+ * Uses the plan's workspace (grown to 13 fields + 1 real field: about 13 times the field's
+ * size) and synchronises the plan's stream.  GP_ERR_NONFINITE if a result is NaN/Inf. */
+gp_status gp_helicity(gp_plan* plan, int field, const void* psi, double* H, double* H_reg, double* spectra, int nbins);
+
 /* Adjoint of nsteps split steps (no counterpart in the paper: the transpose of
  * the Sec. 4.3 step under <a, b> = Re sum conj(a) b).
  *   psi_n:  device field, the state at the start of the nsteps steps (read only);

@@ -52,6 +52,7 @@ SIGNATURES = {
     "gp_phase_grad": (_I, [_P, _I, _P, _P, _P]),
     "gp_diagnostics_noalloc": (_I, [_I, _D, _D, _P, ctypes.POINTER(Diag), ctypes.POINTER(_D), _I, _P]),
     "gp_structure_function": (_I, [_P, _I, _P, _I, ctypes.POINTER(_D), _I]),
+    "gp_helicity": (_I, [_P, _I, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D), _I]),
     "gp_plan_autotune": (_I, [_P, ctypes.c_char_p]),
     "gp_plan_sweep_variant": (_I, [_P, _I, _I, _I]),
     "gp_plan_set_sweep_variant": (_I, [_P, _I, _I, _I, _I]),

@@ -21,20 +21,10 @@
 
 namespace gp {
 
-__device__ __forceinline__ int wavenumber(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
-__device__ __forceinline__ int wavenumber_d(int i, int n) { return (2 * i == n) ? 0 : wavenumber(i, n); }
 
 static inline unsigned rgrid(long long n) {
   long long b = (n + 255) / 256;
   return (unsigned)(b < 1 ? 1 : (b > 152LL * 16 ? 152LL * 16 : b));
-}
-
-// grid coordinates of linear index i (fits in 32 bits: N <= 1024)
-__device__ __forceinline__ void coords3(unsigned i, unsigned n, int& ix, int& iy, int& iz) {
-  const unsigned r = i / n;
-  ix = (int)(i - r * n);
-  iz = (int)(r / n);
-  iy = (int)(r - (unsigned)iz * n);
 }
 
 // sum |psi|^2, sum (|psi|^2 - 1)^2; flags non-finite input
@@ -162,13 +152,6 @@ __device__ __forceinline__ void bin_add(double* hist, int nbins, int b, S (&v)[4
   }
 }
 
-// shell index floor(|k| + 1/2) of the integer |k|^2 = K, exactly: the b with (2b-1)^2 <= 4K < (2b+1)^2
-__device__ __forceinline__ int shell_of(int K) {
-  int b = (int)(sqrtf((float)K) + 0.5f);
-  while ((2 * b + 1) * (2 * b + 1) <= 4 * K) ++b;
-  while (b > 0 && (2 * b - 1) * (2 * b - 1) > 4 * K) --b;
-  return b;
-}
 
 // Helmholtz split and shell binning; spec layout [4][nbins]: E_kin^i, E_kin^c, E_q, E_int (unscaled)
 template <typename T>

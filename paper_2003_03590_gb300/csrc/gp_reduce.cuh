@@ -127,4 +127,24 @@ template <typename T> __device__ __forceinline__ T eps_rho() {
   else return __int_as_float(0x2b8cbccd);
 }
 
+// signed wavenumber of grid index i; the derivative's, with the Nyquist mode set to 0
+__device__ __forceinline__ int wavenumber(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
+__device__ __forceinline__ int wavenumber_d(int i, int n) { return (2 * i == n) ? 0 : wavenumber(i, n); }
+
+// grid coordinates of linear index i (fits in 32 bits: N <= 1024)
+__device__ __forceinline__ void coords3(unsigned i, unsigned n, int& ix, int& iy, int& iz) {
+  const unsigned r = i / n;
+  ix = (int)(i - r * n);
+  iz = (int)(r / n);
+  iy = (int)(r - (unsigned)iz * n);
+}
+
+// shell index floor(|k| + 1/2) of the integer |k|^2 = K, exactly: the b with (2b-1)^2 <= 4K < (2b+1)^2
+__device__ __forceinline__ int shell_of(int K) {
+  int b = (int)(sqrtf((float)K) + 0.5f);
+  while ((2 * b + 1) * (2 * b + 1) <= 4 * K) ++b;
+  while (b > 0 && (2 * b - 1) * (2 * b - 1) > 4 * K) --b;
+  return b;
+}
+
 }  // namespace gp

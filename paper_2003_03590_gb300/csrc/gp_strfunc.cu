@@ -26,18 +26,14 @@ constexpr int SF_R = 8;          // separations per thread
 constexpr int SF_THREADS = 256;
 constexpr int SF_MAX_ORDER = 8;
 
-__device__ __forceinline__ int sf_wavenumber_d(int i, int n) {
-  return (2 * i == n) ? 0 : (i < (n + 1) / 2 ? i : i - n);
-}
-
 // W_j = i k~_j psi_k
 template <typename T>
 __global__ void k_sf_grad(const cpx<T>* __restrict__ ph, cpx<T>* w1, cpx<T>* w2, cpx<T>* w3, int n) {
   const long long npts = (long long)n * n * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
-    const unsigned r = (unsigned)(i / n);
-    const int ix = (int)(i - (long long)r * n), iz = (int)(r / n), iy = (int)(r - (unsigned)iz * n);
-    const T dx = (T)sf_wavenumber_d(ix, n), dy = (T)sf_wavenumber_d(iy, n), dz = (T)sf_wavenumber_d(iz, n);
+    int ix, iy, iz;
+    coords3((unsigned)i, (unsigned)n, ix, iy, iz);
+    const T dx = (T)wavenumber_d(ix, n), dy = (T)wavenumber_d(iy, n), dz = (T)wavenumber_d(iz, n);
     const cpx<T> a = ph[i];
     w1[i] = cpx<T>{-dx * a.y, dx * a.x};
     w2[i] = cpx<T>{-dy * a.y, dy * a.x};

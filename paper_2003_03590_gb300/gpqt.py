@@ -187,6 +187,19 @@ class Plan:
                                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns))
         return out.reshape(3, ns)
 
+    def helicity(self, field, psi, spectra=True):
+        """({"H", "H_reg"}, {"H": H(k), "H_reg": H_reg(k)} or None) of the field (see gp.h)."""
+        h, hr = ctypes.c_double(), ctypes.c_double()
+        nb = self.nbins(field)
+        spec = np.zeros(2 * nb) if spectra else None
+        sp = spec.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if spectra else None
+        self._check(self._lib.gp_helicity(self._h, field, _ptr(self._field(psi, field)), ctypes.byref(h),
+                                          ctypes.byref(hr), sp, nb))
+        out = {"H": h.value, "H_reg": hr.value}
+        if not spectra:
+            return out, None
+        return out, {"H": spec[:nb].copy(), "H_reg": spec[nb:].copy()}
+
     def adjoint_step(self, field, psi_n, lam, nsteps):
         self._check(self._lib.gp_adjoint_step(self._h, field, _ptr(self._field(psi_n, field)),
                                               _ptr(self._field(lam, field)), int(nsteps)))
