@@ -19,6 +19,10 @@ wavenumbers, the Laplacian the full |k|^2; the optional L2 renormalisation (the 
 gradient flow the section starts from) rescales phi after each step to a prescribed mean
 |phi|^2.
 
+Stopping (eqn:crit1, eqn:crit2): ||phi^{n+1} - phi^n||_inf / dtau <= eps, and the relative
+energy change |E_v(phi^{n+1}) - E_v(phi^n)| / (dtau E_v(phi^n)), which the paper reports when
+the first criterion was not reached.
+
 Energy of the driven field (eq-energy-num-ext-vel), as a volume mean:
     E_v = < 2 alpha^2 |grad phi - i v phi / (2 alpha)|^2 + alpha beta (|phi|^2 - 1)^2 >.
 
@@ -197,3 +201,31 @@ def energy_v(phi, alpha, beta, v):
 def residual_inf(phi_new, phi_old, dtau):
     """||phi^{n+1} - phi^n||_inf / dtau (eqn:crit1)."""
     return float(np.max(np.abs(phi_new - phi_old))) / dtau
+
+
+def energy_change(phi_new, phi_old, alpha, beta, dtau, v):
+    """|E_v(phi^{n+1}) - E_v(phi^n)| / (dtau E_v(phi^n)) (eqn:crit2)."""
+    e_old = energy_v(phi_old, alpha, beta, v)
+    return abs(energy_v(phi_new, alpha, beta, v) - e_old) / (dtau * e_old)
+
+
+def argle_converge(phi, alpha, beta, dtau, max_steps, v, eps, check_every, renorm=None):
+    """Steps until eqn:crit1 holds at a checked step or max_steps are done.
+
+    The criteria are evaluated for every check_every-th step and for the last step; the run
+    stops after the first checked step with crit1 <= eps (eps <= 0: never).  Returns
+    (phi, steps_done, crit1, crit2) with the criteria of the last checked step."""
+    c1 = c2 = float("nan")
+    done = 0
+    while done < max_steps:
+        new = argle_step(phi, alpha, beta, dtau, v, renorm)
+        done += 1
+        if done % check_every == 0 or done == max_steps:
+            c1 = residual_inf(new, phi, dtau)
+            c2 = energy_change(new, phi, alpha, beta, dtau, v)
+            phi = new
+            if eps > 0 and c1 <= eps:
+                break
+        else:
+            phi = new
+    return phi, done, c1, c2

@@ -209,3 +209,37 @@ def test_abc_ansatz_phase_is_periodic_and_follows_the_flow():
         assert np.all(np.abs(g[smooth] - v[j][smooth] / (2 * alpha)) <= 2.0 + 1e-6)
         checked += int(smooth.sum())
     assert checked > 550
+
+
+def test_stopping_criteria_of_a_decaying_mode():
+    """beta = 0, v = 0, phi = A exp(i k.x): one step multiplies A by f = (1 - a)/(1 + a), so
+    crit1 = |f - 1| |A| / dtau and, with E_v = 2 alpha^2 |A|^2 |k|^2, crit2 = |f^2 - 1| / dtau."""
+    n, alpha, dtau, A = 12, 0.3, 0.05, 0.8 - 0.3j
+    k = (2, -1, 3)
+    X, Y, Z = OA.coords(n)
+    phi = A * np.exp(1j * (k[0] * X + k[1] * Y + k[2] * Z))
+    a = 0.5 * dtau * alpha * sum(c * c for c in k)
+    f = (1 - a) / (1 + a)
+    new = OA.argle_step(phi, alpha, 0.0, dtau, _zero_v(n))
+    assert OA.residual_inf(new, phi, dtau) == pytest.approx(abs(f - 1) * abs(A) / dtau, rel=1e-12)
+    assert OA.energy_change(new, phi, alpha, 0.0, dtau, _zero_v(n)) == pytest.approx(abs(f * f - 1) / dtau, rel=1e-10)
+
+
+def test_converge_stops_at_the_first_checked_step_below_eps():
+    """The same decaying mode: crit1 after step m is |f - 1| |f|^(m-1) |A| / dtau, a geometric
+    sequence, so the first checked step below eps is known in closed form; eps <= 0 runs all
+    steps and reports the last step's criteria; the stepped field is the plain loop's."""
+    n, alpha, dtau, A = 8, 0.3, 0.05, 1.0
+    k = (1, 2, 0)
+    X, Y, Z = OA.coords(n)
+    phi = A * np.exp(1j * (k[0] * X + k[1] * Y + k[2] * Z))
+    a = 0.5 * dtau * alpha * sum(c * c for c in k)
+    f = (1 - a) / (1 + a)
+    c1 = lambda m: abs(f - 1) * abs(f) ** (m - 1) * A / dtau
+    eps = 0.5 * (c1(23) + c1(24))          # first step with crit1 <= eps is 24; checked every 5: 25
+    out, done, r1, r2 = OA.argle_converge(phi, alpha, 0.0, dtau, 100, _zero_v(n), eps, 5)
+    assert done == 25
+    assert r1 == pytest.approx(c1(25), rel=1e-10) and r2 == pytest.approx(abs(f * f - 1) / dtau, rel=1e-8)
+    assert np.max(np.abs(out - OA.argle(phi, alpha, 0.0, dtau, 25, _zero_v(n)))) == 0.0
+    out, done, r1, _ = OA.argle_converge(phi, alpha, 0.0, dtau, 13, _zero_v(n), 0.0, 5)
+    assert done == 13 and r1 == pytest.approx(c1(13), rel=1e-10)
