@@ -267,6 +267,19 @@ gp_status gp_init_abc(gp_plan* plan, int field, void* psi_dev, const double* abc
 gp_status gp_argle(gp_plan* plan, int field, void* psi_dev, int flow, const double* abc, double dtau, int nsteps,
                    int renorm, double* energy_out);
 
+/* gp_argle_converge: gp_argle with the paper's stopping rules (eqn:crit1, eqn:crit2).  Up to
+ * max_steps >= 1 steps; every check_every-th step (check_every >= 1) and the last one evaluate
+ *   crit1 = ||phi^{n+1} - phi^n||_inf / dtau,
+ *   crit2 = |E_v(phi^{n+1}) - E_v(phi^n)| / (dtau E_v(phi^n)),
+ * and the run stops after the first checked step with crit1 <= eps (eps <= 0: never; run all
+ * steps).  steps_done, crit1, crit2 (host) receive the number of steps taken and the criteria of
+ * the last checked step; energy_out as for gp_argle.  A checked step costs two E_v evaluations
+ * (four transforms each) and a copy of the field, and synchronises the stream; the workspace
+ * grows to five fields. */
+gp_status gp_argle_converge(gp_plan* plan, int field, void* psi_dev, int flow, const double* abc, double dtau,
+                            int max_steps, int renorm, double eps, int check_every, int* steps_done, double* crit1,
+                            double* crit2, double* energy_out);
+
 /* Waits for the plan's stream and reads the device status word that the persistent sweep
  * kernels set when one of their bounded waits (a TMA copy, a tile counter of the fused plane
  * kernel) gives up instead of hanging.  GP_OK if none did since the last check; otherwise

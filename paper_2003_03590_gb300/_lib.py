@@ -60,6 +60,8 @@ SIGNATURES = {
     "gp_init_tg": (_I, [_P, _I, _P]),
     "gp_init_abc": (_I, [_P, _I, _P, _P]),
     "gp_argle": (_I, [_P, _I, _P, _I, _P, ctypes.c_double, _I, _I, _P]),
+    "gp_argle_converge": (_I, [_P, _I, _P, _I, _P, ctypes.c_double, _I, _I, ctypes.c_double, _I,
+                               ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "gp_plan_test_timeout": (_I, [_P, _I]),
     "gp_profile": (_I, [_P, _I]),
     "gp_profile_read": (_I, [_P, _I, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D)]),

@@ -245,25 +245,78 @@ template <typename T> static cudaError_t transform(gp_plan* p, FieldPlan& F, cpx
   return cudaSuccess;
 }
 
+// per-block maxima of |phi - old|^2 (a maximum is exact in any precision)
+template <typename T>
+__global__ void k_maxdiff2(const cpx<T>* __restrict__ phi, const cpx<T>* __restrict__ old, long long npts, double* part) {
+  T m = T(0);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
+    const cpx<T> a = phi[i], b = old[i];
+    const T dx = a.x - b.x, dy = a.y - b.y, d2 = dx * dx + dy * dy;
+    m = d2 > m ? d2 : m;
+  }
+  double md = (double)m;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = md;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) md = fmax(md, red[q]);
+    part[blockIdx.x] = md;
+  }
+}
+
+// Convergence checks of a run (eqn:crit1, eqn:crit2): every `every`-th step and the last one
+// evaluate ||phi^{n+1} - phi^n||_inf / dtau and |E_v(phi^{n+1}) - E_v(phi^n)| / (dtau E_v(phi^n));
+// the run stops after the first checked step with crit1 <= eps (eps <= 0: never).
+struct ArgleCheck {
+  int every = 0;   // 0: no checks
+  double eps = 0.0;
+  int* steps_done = nullptr;
+  double* crit1 = nullptr;
+  double* crit2 = nullptr;
+};
+
 template <typename T>
 static gp_status argle_impl(gp_plan* p, int field, cpx<T>* phi, Flow flow, double dtau, int nsteps, int renorm,
-                            double* energy_out) {
+                            double* energy_out, const ArgleCheck& chk = ArgleCheck()) {
   FieldPlan& F = p->f[field];
   const int n = F.n;
   const long long npts = F.npts;
   const size_t fb = (size_t)npts * sizeof(cpx<T>);
   const unsigned g = agrid(npts);
-  gp_status st = ensure_ws(p, field, 4 * fb + (size_t)(2 * g + 8) * sizeof(double));
+  const int nf = chk.every > 0 ? 5 : 4;
+  gp_status st = ensure_ws(p, field, nf * fb + (size_t)(2 * g + 16) * sizeof(double));
   if (st != GP_OK) return st;
   cpx<T>* ph = (cpx<T>*)F.ws;
   cpx<T>* w1 = ph + npts;
   cpx<T>* w2 = w1 + npts;
   cpx<T>* w3 = w2 + npts;
-  double* part = (double*)(w3 + npts);
-  double* red = part + 2 * g;   // [0] mass sum, [1] target mean |phi|^2, [2..3] energy sums
+  cpx<T>* old = w3 + npts;                       // the field before a checked step
+  double* part = (double*)(ph + (size_t)nf * npts);
+  // red: [0] mass sum, [1] target mean |phi|^2, [2..3] energy sums, [4..5] E_v sums before and
+  // [6..7] after a checked step, [8] max |phi^{n+1} - phi^n|^2
+  double* red = part + 2 * g;
   cudaStream_t s = p->stream;
-  const double alpha = F.alpha, beta = F.beta;
+  const double alpha = F.alpha, beta = F.beta, dn = (double)npts;
   cpx<T>* grads[3] = {w1, w2, w3};
+  // E_v sums of the current phi into dst[0..1] (enqueued only; uses w1..w3)
+  auto energy_sums = [&](double* dst) -> gp_status {
+    GP_CUDA(p, cudaMemcpyAsync(w1, phi, fb, cudaMemcpyDeviceToDevice, s));
+    GP_CUDA(p, transform<T>(p, F, &w1, 1, false, s));
+    k_grad_spec<T><<<g, 256, 0, s>>>(w1, w1, w2, w3, n);   // in place: w1 is read before it is written
+    GP_CUDA(p, cudaGetLastError());
+    GP_CUDA(p, transform<T>(p, F, grads, 3, true, s));
+    k_energy_v<T><<<g, 256, 0, s>>>(phi, w1, w2, w3, n, flow, alpha, part);
+    k_reduce<<<1, 256, 0, s>>>(part, (int)g, 2, dst);
+    GP_CUDA(p, cudaGetLastError());
+    return GP_OK;
+  };
+  auto energy_of = [&](const double* e) { return 2.0 * alpha * alpha * e[0] / dn + alpha * beta * e[1] / dn; };
+  if (chk.every > 0) {
+    *chk.steps_done = 0;
+    *chk.crit1 = *chk.crit2 = std::nan("");
+  }
   if (nsteps > 0) {
     if (renorm) {
       k_mass<T><<<g, 256, 0, s>>>(phi, npts, part);
@@ -274,6 +327,12 @@ static gp_status argle_impl(gp_plan* p, int field, cpx<T>* phi, Flow flow, doubl
     GP_CUDA(p, cudaMemcpyAsync(ph, phi, fb, cudaMemcpyDeviceToDevice, s));
     GP_CUDA(p, transform<T>(p, F, &ph, 1, false, s));
     for (int it = 0; it < nsteps; ++it) {
+      const bool check = chk.every > 0 && ((it + 1) % chk.every == 0 || it + 1 == nsteps);
+      if (check) {
+        GP_CUDA(p, cudaMemcpyAsync(old, phi, fb, cudaMemcpyDeviceToDevice, s));
+        st = energy_sums(red + 4);
+        if (st != GP_OK) return st;
+      }
       k_grad_spec<T><<<g, 256, 0, s>>>(ph, w1, w2, w3, n);
       GP_CUDA(p, cudaGetLastError());
       GP_CUDA(p, transform<T>(p, F, grads, 3, true, s));
@@ -289,17 +348,30 @@ static gp_status argle_impl(gp_plan* p, int field, cpx<T>* phi, Flow flow, doubl
         k_rescale<T><<<g, 256, 0, s>>>(phi, ph, npts, red, red + 1);
         GP_CUDA(p, cudaGetLastError());
       }
+      if (check) {
+        k_maxdiff2<T><<<g, 256, 0, s>>>(phi, old, npts, part + g);
+        k_reduce_max<<<1, 256, 0, s>>>(part + g, (int)g, red + 8);
+        GP_CUDA(p, cudaGetLastError());
+        st = energy_sums(red + 6);
+        if (st != GP_OK) return st;
+        double h[5];
+        GP_CUDA(p, cudaMemcpyAsync(h, red + 4, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GP_CUDA(p, cudaStreamSynchronize(s));
+        st = check_status(p);
+        if (st != GP_OK) return st;
+        const double e_old = energy_of(h), e_new = energy_of(h + 2);
+        *chk.steps_done = it + 1;
+        *chk.crit1 = std::sqrt(h[4]) / dtau;
+        *chk.crit2 = std::fabs(e_new - e_old) / (dtau * e_old);
+        if (!std::isfinite(*chk.crit1) || !std::isfinite(e_new))
+          return fail(p, GP_ERR_NONFINITE, "gp_argle_converge: the field is not finite");
+        if (chk.eps > 0.0 && *chk.crit1 <= chk.eps) break;
+      }
     }
   }
   if (!energy_out) return GP_OK;
-  GP_CUDA(p, cudaMemcpyAsync(w1, phi, fb, cudaMemcpyDeviceToDevice, s));
-  GP_CUDA(p, transform<T>(p, F, &w1, 1, false, s));
-  k_grad_spec<T><<<g, 256, 0, s>>>(w1, w1, w2, w3, n);   // in place: w1 is read before it is written
-  GP_CUDA(p, cudaGetLastError());
-  GP_CUDA(p, transform<T>(p, F, grads, 3, true, s));
-  k_energy_v<T><<<g, 256, 0, s>>>(phi, w1, w2, w3, n, flow, alpha, part);
-  k_reduce<<<1, 256, 0, s>>>(part, (int)g, 2, red + 2);
-  GP_CUDA(p, cudaGetLastError());
+  st = energy_sums(red + 2);
+  if (st != GP_OK) return st;
   double e[2];
   GP_CUDA(p, cudaMemcpyAsync(e, red + 2, sizeof(e), cudaMemcpyDeviceToHost, s));
   GP_CUDA(p, cudaStreamSynchronize(s));
@@ -307,8 +379,7 @@ static gp_status argle_impl(gp_plan* p, int field, cpx<T>* phi, Flow flow, doubl
     gp_status cs = check_status(p);
     if (cs != GP_OK) return cs;
   }
-  const double dn = (double)npts;
-  *energy_out = 2.0 * alpha * alpha * e[0] / dn + alpha * beta * e[1] / dn;
+  *energy_out = energy_of(e);
   if (!std::isfinite(*energy_out)) return fail(p, GP_ERR_NONFINITE, "gp_argle: energy is not finite");
   return GP_OK;
 }
@@ -367,6 +438,30 @@ gp_status gp_argle(gp_plan* p, int field, void* psi, int flow, const double* abc
   FieldPlan& F = p->f[field];
   if (F.fp64) return argle_impl<double>(p, field, (cpx<double>*)psi, f, dtau, nsteps, renorm, energy_out);
   return argle_impl<float>(p, field, (cpx<float>*)psi, f, dtau, nsteps, renorm, energy_out);
+}
+
+gp_status gp_argle_converge(gp_plan* p, int field, void* psi, int flow, const double* abc, double dtau, int max_steps,
+                            int renorm, double eps, int check_every, int* steps_done, double* crit1, double* crit2,
+                            double* energy_out) {
+  if (!p) return GP_ERR_INVALID_ARG;
+  if (field < 0 || field >= (int)p->f.size()) return fail(p, GP_ERR_INVALID_ARG, "gp_argle_converge: field index");
+  if (!psi || ((uintptr_t)psi & 15) || !steps_done || !crit1 || !crit2)
+    return fail(p, GP_ERR_INVALID_ARG, "gp_argle_converge: pointer");
+  if (max_steps < 1 || check_every < 1 || !(dtau > 0.0) || !std::isfinite(dtau) || !std::isfinite(eps) ||
+      (renorm != 0 && renorm != 1))
+    return fail(p, GP_ERR_INVALID_ARG, "gp_argle_converge: max_steps >= 1, check_every >= 1, dtau > 0, renorm 0 or 1");
+  Flow f;
+  if (!flow_of(flow, abc, &f))
+    return fail(p, GP_ERR_INVALID_ARG, "gp_argle_converge: flow must be 0 (none), 1 (TG) or 2 (ABC)");
+  ArgleCheck chk;
+  chk.every = check_every;
+  chk.eps = eps;
+  chk.steps_done = steps_done;
+  chk.crit1 = crit1;
+  chk.crit2 = crit2;
+  FieldPlan& F = p->f[field];
+  if (F.fp64) return argle_impl<double>(p, field, (cpx<double>*)psi, f, dtau, max_steps, renorm, energy_out, chk);
+  return argle_impl<float>(p, field, (cpx<float>*)psi, f, dtau, max_steps, renorm, energy_out, chk);
 }
 
 }  // extern "C"

@@ -129,6 +129,18 @@ class Plan:
                                        int(nsteps), 1 if renorm else 0, ctypes.byref(e) if energy else None))
         return e.value if energy else None
 
+    def argle_converge(self, field, psi, flow, dtau, max_steps, eps, check_every=100, abc=None, renorm=False,
+                       energy=True):
+        """ARGLE steps in place until ||phi^{n+1} - phi^n||_inf / dtau <= eps at a checked step (every
+        check_every steps and the last) or max_steps; returns (steps_done, crit1, crit2, E_v or None)."""
+        ptr, _keep = self._abc_arg(abc)
+        done, c1, c2, e = ctypes.c_int(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.gp_argle_converge(self._h, field, _ptr(self._field(psi, field)), int(flow), ptr,
+                                                float(dtau), int(max_steps), 1 if renorm else 0, float(eps),
+                                                int(check_every), ctypes.byref(done), ctypes.byref(c1),
+                                                ctypes.byref(c2), ctypes.byref(e) if energy else None))
+        return done.value, c1.value, c2.value, (e.value if energy else None)
+
     def psi_from_phase(self, field, theta, out=None):
         if out is None:
             out = self.empty(field)

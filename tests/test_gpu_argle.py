@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from paper_2003_03590_gb300 import GP_FP32, GP_FP64, Plan, field_params  # noqa: E402
+from paper_2003_03590_gb300 import GP_FP32, GP_FP64, GPError, Plan, field_params  # noqa: E402
 from paper_2003_03590_gb300.gpqt import GP_FLOW_ABC, GP_FLOW_NONE, GP_FLOW_TG  # noqa: E402
 
 KIND = {GP_FLOW_NONE: "none", GP_FLOW_TG: "tg", GP_FLOW_ABC: "abc"}
@@ -68,6 +68,45 @@ def test_argle_steps_match_oracle(flow, prec, renorm):
     tol = 1e-11 if prec == GP_FP64 else 2e-5
     assert rel_l2(to_np(psi), ref) < tol
     assert abs(e - OA.energy_v(ref, alpha, beta, v)) < tol * abs(e)
+
+
+@pytest.mark.parametrize("prec", [GP_FP64, GP_FP32])
+@pytest.mark.parametrize("flow", [GP_FLOW_NONE, GP_FLOW_TG, GP_FLOW_ABC])
+def test_argle_stopping_criteria_match_oracle(flow, prec):
+    """eqn:crit1 / eqn:crit2 of the last checked step, the step count and the field, against the
+    oracle's checked loop: once running to max_steps (eps = 0), once stopping at the checked step
+    where the residual first falls below an eps placed between two of the oracle's values."""
+    n, dtau, alpha, beta = 24, 0.0125, 0.2, 10.0
+    plan = _plan(n, prec, alpha, beta)
+    phi0 = smooth_psi(n, 23).astype(_dtype(prec))
+    v = OA.velocity(KIND[flow], n)
+    tol = 1e-10 if prec == GP_FP64 else 1e-4
+    psi = to_gpu(phi0, _dtype(prec))
+    done, c1, c2, e = plan.argle_converge(0, psi, flow, dtau, 7, 0.0, check_every=3)
+    ref, rdone, r1, r2 = OA.argle_converge(phi0.astype(np.complex128), alpha, beta, dtau, 7, v, 0.0, 3)
+    assert done == rdone == 7
+    assert c1 == pytest.approx(r1, rel=tol) and c2 == pytest.approx(r2, rel=10 * tol)
+    assert rel_l2(to_np(psi), ref) < (1e-11 if prec == GP_FP64 else 2e-5)
+    assert e == pytest.approx(OA.energy_v(ref, alpha, beta, v), rel=tol)
+    # the oracle's residuals at the checks 2, 4, ..., 12; eps between the smallest of the first k
+    # and a smaller k+1-th, so the first check at or below eps is the (k+1)-th
+    seq = [OA.argle_converge(phi0.astype(np.complex128), alpha, beta, dtau, m, v, 0.0, 2)[2] for m in range(2, 13, 2)]
+    k = next(j for j in range(1, len(seq)) if seq[j] < 0.999 * min(seq[:j]))
+    eps = 0.5 * (min(seq[:k]) + seq[k])
+    psi = to_gpu(phi0, _dtype(prec))
+    done, c1, _, _ = plan.argle_converge(0, psi, flow, dtau, 40, eps, check_every=2, energy=False)
+    assert done == 2 * (k + 1) and c1 <= eps
+
+
+def test_argle_converge_rejects_bad_arguments():
+    plan = _plan(16, GP_FP32)
+    psi = torch.ones((16, 16, 16), dtype=torch.complex64, device="cuda")
+    for kw in ({"max_steps": 0}, {"check_every": 0}, {"dtau": -1.0}):
+        args = {"dtau": 0.01, "max_steps": 5, "check_every": 1}
+        args.update(kw)
+        with pytest.raises(GPError):
+            plan.argle_converge(0, psi, GP_FLOW_NONE, args["dtau"], args["max_steps"], 1e-3,
+                                check_every=args["check_every"])
 
 
 def test_argle_energy_of_a_plane_wave_in_its_flow_is_zero():
