@@ -31,6 +31,11 @@ template <typename T> using cpx = typename CT<T>::v;
 
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
+// float32: one packed FP32x2 instruction per complex operation.  Each lane rounds exactly as the
+// scalar operation would (b * -1 is exact, so fma(b, -1, a) is a - b rounded once).
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, float2{-1.0f, -1.0f}, a); }
+__device__ __forceinline__ float2 swap2(float2 a) { return float2{a.y, a.x}; }
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
   return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
@@ -38,6 +43,7 @@ template <typename V> __device__ __forceinline__ V cmulconj(V a, V b) {  // a * 
   return V{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
 template <typename V, typename S> __device__ __forceinline__ V cscale(V a, S s) { return V{a.x * s, a.y * s}; }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return __fmul2_rn(a, float2{s, s}); }
 template <typename V> __device__ __forceinline__ V cneg(V a) { return V{-a.x, -a.y}; }
 // a * (-i) for the forward direction, a * (+i) for the inverse one
 template <bool INV, typename V> __device__ __forceinline__ V mul_mi(V a) {
@@ -59,19 +65,26 @@ __host__ __device__ constexpr KConst kconst(double v) {
 }
 __device__ __forceinline__ float kmul(float x, KConst k) { return fmaf(x, k.hi, x * k.lo); }
 __device__ __forceinline__ double kmul(double x, KConst k) { return x * k.v; }
+// both lanes of a float2 times the constants sa * k (lane 0) and sb * k (lane 1), sa, sb = +-1:
+// per lane fma(x, +-hi, x * +-lo), the negation of kmul(x, k) when the sign is -1
+__device__ __forceinline__ float2 kmul2(float2 x, KConst k, float sa, float sb) {
+  return __ffma2_rn(x, float2{sa * k.hi, sb * k.hi}, __fmul2_rn(x, float2{sa * k.lo, sb * k.lo}));
+}
 
 // a * (c - i s) forward, a * (c + i s) inverse, for constants c = cos(theta), s = sin(theta)
 // (float: every product-sum is an explicit fma, so that the rounding does not depend on how the
 // compiler would contract a*b + c*d in a given kernel -- all kernel variants agree bitwise)
-template <bool INV, typename V> __device__ __forceinline__ V rotk(V a, KConst c, KConst s) {
+// NEG: the negated product (float: the constants negated, which rounds to exactly the negation).
+template <bool INV, typename V, bool NEG = false> __device__ __forceinline__ V rotk(V a, KConst c, KConst s) {
   if constexpr (sizeof(a.x) == 4) {
-    const float re_lo = fmaf(a.x, c.lo, (INV ? -a.y : a.y) * s.lo);
-    const float im_lo = fmaf(a.y, c.lo, (INV ? a.x : -a.x) * s.lo);
-    const float re = fmaf(a.x, c.hi, fmaf(INV ? -a.y : a.y, s.hi, re_lo));
-    const float im = fmaf(a.y, c.hi, fmaf(INV ? a.x : -a.x, s.hi, im_lo));
-    return V{re, im};
+    // lanes (re, im): lo = a c.lo + (+-a.y, -+a.x) s.lo;  result = a c.hi + ((+-a.y, -+a.x) s.hi + lo)
+    const float2 b = swap2(a);
+    const float sg = INV ? -1.0f : 1.0f, ng = NEG ? -1.0f : 1.0f;
+    const float2 lo = __ffma2_rn(a, float2{ng * c.lo, ng * c.lo}, __fmul2_rn(b, float2{ng * sg * s.lo, -ng * sg * s.lo}));
+    return __ffma2_rn(a, float2{ng * c.hi, ng * c.hi}, __ffma2_rn(b, float2{ng * sg * s.hi, -ng * sg * s.hi}, lo));
   } else {
-    return INV ? V{a.x * c.v - a.y * s.v, a.y * c.v + a.x * s.v} : V{a.x * c.v + a.y * s.v, a.y * c.v - a.x * s.v};
+    const V r = INV ? V{a.x * c.v - a.y * s.v, a.y * c.v + a.x * s.v} : V{a.x * c.v + a.y * s.v, a.y * c.v - a.x * s.v};
+    return NEG ? cneg(r) : r;
   }
 }
 // multiplication by exp(-+ i pi/4) and exp(-+ 3 i pi/4): one constant, 1/sqrt(2)
@@ -80,10 +93,22 @@ constexpr KConst K_C16 = kconst(0.92387953251128675613);   // cos(pi/8)
 constexpr KConst K_S16 = kconst(0.38268343236508977173);   // sin(pi/8)
 constexpr KConst K_H3 = kconst(0.86602540378443864676);    // sqrt(3)/2
 template <bool INV, typename V> __device__ __forceinline__ V rot45(V a) {   // * exp(-+ i pi/4)
-  return INV ? V{kmul(a.x - a.y, K_R2), kmul(a.x + a.y, K_R2)} : V{kmul(a.x + a.y, K_R2), kmul(a.y - a.x, K_R2)};
+  if constexpr (sizeof(a.x) == 4) {
+    // forward (a.x + a.y, -(a.x - a.y)) K;  inverse (a.x - a.y, a.x + a.y) K
+    if constexpr (INV) return kmul2(__ffma2_rn(swap2(a), float2{-1.0f, 1.0f}, a), K_R2, 1.0f, 1.0f);
+    else return kmul2(__ffma2_rn(a, float2{1.0f, -1.0f}, swap2(a)), K_R2, 1.0f, -1.0f);
+  } else {
+    return INV ? V{kmul(a.x - a.y, K_R2), kmul(a.x + a.y, K_R2)} : V{kmul(a.x + a.y, K_R2), kmul(a.y - a.x, K_R2)};
+  }
 }
 template <bool INV, typename V> __device__ __forceinline__ V rot135(V a) {  // * exp(-+ 3 i pi/4)
-  return INV ? V{kmul(-a.x - a.y, K_R2), kmul(a.x - a.y, K_R2)} : V{kmul(a.y - a.x, K_R2), kmul(-a.x - a.y, K_R2)};
+  if constexpr (sizeof(a.x) == 4) {
+    // forward (a.y - a.x, -(a.x + a.y)) K;  inverse (-(a.x + a.y), a.x - a.y) K
+    if constexpr (INV) return kmul2(__ffma2_rn(a, float2{1.0f, -1.0f}, swap2(a)), K_R2, -1.0f, 1.0f);
+    else return kmul2(__ffma2_rn(a, float2{-1.0f, 1.0f}, swap2(a)), K_R2, 1.0f, -1.0f);
+  } else {
+    return INV ? V{kmul(-a.x - a.y, K_R2), kmul(a.x - a.y, K_R2)} : V{kmul(a.y - a.x, K_R2), kmul(-a.x - a.y, K_R2)};
+  }
 }
 
 // Stockham twiddle storage: float32 keeps hi (x, y) and lo (z, w) parts, float64 the value.
@@ -126,20 +151,39 @@ template <bool INV, typename V> __device__ __forceinline__ void dft2(V& a, V& b)
   b = csub(t, b);
 }
 
+// p = e + m, q = e - m with m = -+i o (forward -i, inverse +i)
+template <bool INV, typename V> __device__ __forceinline__ void add_sub_mi(V e, V o, V& p, V& q) {
+  if constexpr (sizeof(e.x) == 4) {
+    // -i o = (o.y, -o.x), i o = (-o.y, o.x): both lanes from the swapped o with signs
+    const float2 os = swap2(o);
+    p = __ffma2_rn(os, INV ? float2{-1.0f, 1.0f} : float2{1.0f, -1.0f}, e);
+    q = __ffma2_rn(os, INV ? float2{1.0f, -1.0f} : float2{-1.0f, 1.0f}, e);
+  } else {
+    const V m = mul_mi<INV>(o);
+    p = cadd(e, m);
+    q = csub(e, m);
+  }
+}
+
 template <bool INV, typename V> __device__ __forceinline__ void dft4(V& a0, V& a1, V& a2, V& a3) {
-  V s0 = cadd(a0, a2), d0 = csub(a0, a2), s1 = cadd(a1, a3), d1 = mul_mi<INV>(csub(a1, a3));
+  V s0 = cadd(a0, a2), d0 = csub(a0, a2), s1 = cadd(a1, a3), d1 = csub(a1, a3);
   a0 = cadd(s0, s1);
   a2 = csub(s0, s1);
-  a1 = cadd(d0, d1);
-  a3 = csub(d0, d1);
+  add_sub_mi<INV>(d0, d1, a1, a3);
 }
 
 template <bool INV, typename V> __device__ __forceinline__ void dft3(V& a0, V& a1, V& a2) {
   using S = decltype(a0.x);
   V t1 = cadd(a1, a2);
-  V t2 = V{a0.x - S(0.5) * t1.x, a0.y - S(0.5) * t1.y};
   V d = csub(a1, a2);
-  V t3 = V{kmul(d.x, K_H3), kmul(d.y, K_H3)};   // (a1 - a2) sqrt(3)/2
+  V t2, t3;
+  if constexpr (sizeof(S) == 4) {
+    t2 = __ffma2_rn(t1, float2{-0.5f, -0.5f}, a0);   // a0 - t1 / 2 (the product is exact)
+    t3 = kmul2(d, K_H3, 1.0f, 1.0f);                  // (a1 - a2) sqrt(3)/2
+  } else {
+    t2 = V{a0.x - S(0.5) * t1.x, a0.y - S(0.5) * t1.y};
+    t3 = V{kmul(d.x, K_H3), kmul(d.y, K_H3)};
+  }
   V it3 = V{-t3.y, t3.x};  // i t3
   a0 = cadd(a0, t1);
   if (!INV) { a1 = csub(t2, it3); a2 = cadd(t2, it3); }
@@ -152,11 +196,10 @@ template <bool INV, typename V> __device__ __forceinline__ void dft8(V* v) {
   dft4<INV>(e0, e1, e2, e3);
   dft4<INV>(o0, o1, o2, o3);
   o1 = rot45<INV>(o1);          // w8^1
-  o2 = mul_mi<INV>(o2);         // w8^2
   o3 = rot135<INV>(o3);         // w8^3
   v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
   v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
-  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+  add_sub_mi<INV>(e2, o2, v[2], v[6]);   // w8^2 = -+i
   v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
 }
 
@@ -173,7 +216,7 @@ template <bool INV, typename V> __device__ __forceinline__ void dft16(V* v) {
   v[11] = rot135<INV>(v[11]);              // n2=3,k1=2: w^6
   v[13] = rotk<INV>(v[13], K_S16, K_C16);  // n2=1,k1=3: w^3
   v[14] = rot135<INV>(v[14]);              // n2=2,k1=3: w^6
-  v[15] = cneg(rotk<INV>(v[15], K_C16, K_S16));  // n2=3,k1=3: w^9 = -w^1
+  v[15] = rotk<INV, V, true>(v[15], K_C16, K_S16);  // n2=3,k1=3: w^9 = -w^1
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
   // v[4 k1 + k2] = X[k1 + 4 k2]: transpose to natural order
