@@ -328,6 +328,23 @@ def diag_leg(gq, plan, psi, n, ms_step, calls=3):
     return {"ms_per_call": ms, "share_at_1_per_100_steps": ms / (ms + 100 * ms_step)}
 
 
+def analysis_leg(plan, psi, calls=3):
+    """Wall time per call of the field analyses on the timed field: the second-order structure
+    functions along x, y, z (Sec. 3.5) and both helicities with their spectra (Sec. 3.6); each
+    call synchronises the stream."""
+    import torch
+    out = {}
+    for name, fn in (("structure_function_p2", lambda: plan.structure_function(0, psi, 2)),
+                     ("helicity_with_spectra", lambda: plan.helicity(0, psi))):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(calls):
+            fn()
+        out[name] = {"ms_per_call": (time.perf_counter() - t0) * 1e3 / calls}
+    return out
+
+
 def argle_leg(gq, steps=200):
     """Imaginary-time (ARGLE) preparation of the paper's 128^3 Taylor-Green run (alpha = 0.05,
     beta = 40, dtau = 1.25e-2): time per ARGLE step (five 3D transforms) in float32 and float64."""
@@ -512,6 +529,7 @@ def main():
         extras["ensemble"] = ensemble_leg(gq)
         extras["adjoint_128"] = adjoint_leg(gq)
         extras["diagnostics_cost"] = diag_leg(gq, plan, psi, n, ms_step)
+        extras["analysis_cost"] = analysis_leg(plan, psi)
         extras["argle_tg_128"] = argle_leg(gq)
         # the float64 oracle on the host cores: one full step of the same 256^3 workload
         val, secs = cpu_oracle_baseline(n, DT_MAIN, 1)
