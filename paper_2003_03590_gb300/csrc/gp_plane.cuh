@@ -359,13 +359,15 @@ template <int L> struct TmaPlaneLaunch {
     }
     return occ;
   }
-  // grid for a launch over `count` fields (the lag depends on it)
-  template <int NS> static int grid(int count) {
+  // grid for a launch over `count` fields (the lag depends on it); cap > 0 limits the CTAs per SM
+  template <int NS> static int grid(int count, int cap) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int items = 3 * count * L * TmaPlane<L, NS>::Q;
-    int g = sms * (occupancy<NS>() > 0 ? occupancy<NS>() : 1);
+    int per = occupancy<NS>() > 0 ? occupancy<NS>() : 1;
+    if (cap > 0 && cap < per) per = cap;
+    const int g = sms * per;
     return g > items ? items : g;
   }
   // Tickets in flight: each CTA holds up to S loaded items, the rest of a chunk and the item
@@ -377,15 +379,16 @@ template <int L> struct TmaPlaneLaunch {
     constexpr int per_plane = 3 * TmaPlane<L, NS>::Q;
     return (2 * grid * (TmaPlane<L, NS>::S + TmaPlane<L, NS>::CHUNK + 1) + per_plane - 1) / per_plane + 1;
   }
-  template <int NS> static cudaError_t run(TmaPlaneArgs& a, cudaStream_t s) {
+  template <int NS> static cudaError_t run(TmaPlaneArgs& a, int cap, cudaStream_t s) {
     if (occupancy<NS>() < 1) return cudaErrorInvalidConfiguration;
-    const int g = grid<NS>(a.count);
+    const int g = grid<NS>(a.count, cap);
     a.lag = lag<NS>(g);
     k_tma_plane<L, NS><<<g, TmaPlane<L, NS>::NT, TmaPlane<L, NS>::SMEM, s>>>(a);
     return cudaGetLastError();
   }
-  static cudaError_t launch(TmaPlaneArgs& a, int stages, cudaStream_t s) {
-    return stages == 2 ? run<2>(a, s) : run<3>(a, s);
+  // stages: 2 or 3 shared-memory stages; ctas_per_sm: 0 = as many as fit, else at most that many
+  static cudaError_t launch(TmaPlaneArgs& a, int stages, int ctas_per_sm, cudaStream_t s) {
+    return stages == 2 ? run<2>(a, ctas_per_sm, s) : run<3>(a, ctas_per_sm, s);
   }
 };
 

@@ -18,7 +18,8 @@ if not torch.cuda.is_available():
 
 from paper_2003_03590_gb300 import (GP_FP32, GP_FP64, GP_SPLIT_KNK, GP_SPLIT_NKN, GPEvolve,  # noqa: E402
                                     IncompressibleKineticEnergy, Plan, field_params)
-from paper_2003_03590_gb300.gpqt import OP_PLANE, VARIANT_PLAIN, VARIANT_TMA, VARIANT_TMA_2STAGE  # noqa: E402
+from paper_2003_03590_gb300.gpqt import (OP_PLANE, VARIANT_PLAIN, VARIANT_TMA, VARIANT_TMA_2STAGE,  # noqa: E402
+                                         VARIANT_TMA_ONE)
 
 
 def _op(plan, dt):
@@ -127,23 +128,28 @@ def test_fused_plane_kernel_matches_separate_sweeps_bitwise(split):
     sizes = [32, 32, 48, 64, 96, 128, 192, 256]
     fused = Plan([field_params(n, dt, xi_over_dx=1.5, split=split) for n in sizes])
     two = Plan([field_params(n, dt, xi_over_dx=1.5, split=split) for n in sizes])
+    one = Plan([field_params(n, dt, xi_over_dx=1.5, split=split) for n in sizes])
     sep = Plan([field_params(n, dt, xi_over_dx=1.5, split=split) for n in sizes])
     for n in set(sizes):
         assert fused.sweep_variant(n, 1, OP_PLANE) == VARIANT_TMA       # the default
         two.set_sweep_variant(n, 1, OP_PLANE, VARIANT_TMA_2STAGE)      # two stages, twiddles via L1
+        one.set_sweep_variant(n, 1, OP_PLANE, VARIANT_TMA_ONE)         # one CTA per SM (another lag)
         sep.set_sweep_variant(n, 1, OP_PLANE, VARIANT_PLAIN)
     fa = [to_gpu(random_psi(n, 70 + i), np.complex64) for i, n in enumerate(sizes)]
     fb = [f.clone() for f in fa]
     fc = [f.clone() for f in fa]
+    fd = [f.clone() for f in fa]
     for steps in (5, 9):                    # the second call replays the captured cycle
         fused.step(fa, steps)
         sep.step(fb, steps)
         two.step(fc, steps)
-        for p in (fused, sep, two):
+        one.step(fd, steps)
+        for p in (fused, sep, two, one):
             p.sync()                        # no bounded wait gave up
-        for i, (x, y, z) in enumerate(zip(fa, fb, fc)):
+        for i, (x, y, z, w) in enumerate(zip(fa, fb, fc, fd)):
             assert torch.equal(x, y), sizes[i]
             assert torch.equal(z, y), sizes[i]
+            assert torch.equal(w, y), sizes[i]
 
 
 def test_bounded_wait_gives_up_and_reports_timeout():
@@ -269,7 +275,7 @@ def test_autotune_picks_variants_and_caches(tmp_path):
         for axis, op in ((2, 3), (1, 1), (1, 2)):
             assert tuned.sweep_variant(n, axis, op) in (0, 1, 2, 3)
         assert tuned.sweep_variant(n, 0, 6) in (0, 1, 2)
-        assert tuned.sweep_variant(n, 1, OP_PLANE) in (VARIANT_TMA, VARIANT_PLAIN)
+        assert tuned.sweep_variant(n, 1, OP_PLANE) in (VARIANT_TMA, VARIANT_TMA_ONE, VARIANT_PLAIN, VARIANT_TMA_2STAGE)
     again = Plan([field_params(n, dt, xi_over_dx=1.5) for n in sizes]).autotune(cache)   # from the cache
     for n in sizes:
         assert again.sweep_variant(n, 0, 6) == tuned.sweep_variant(n, 0, 6)
