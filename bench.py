@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--only-step", action="store_true", help="init, warm-up and the timed steps only (profiling)")
     ap.add_argument("--only-diag", type=int, default=0, metavar="CALLS",
                     help="init, then CALLS diagnostics calls of the step workload's field (profiling)")
+    ap.add_argument("--kernel-tour", action="store_true",
+                    help="every library entry point once on the benchmark's sizes, then exit (for a per-kernel ncu list)")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of kernel choices: read if present (no tuning launches), else written")
     return ap.parse_args()
@@ -345,6 +347,54 @@ def analysis_leg(plan, psi, calls=3):
     return out
 
 
+def kernel_tour(gq):
+    """Every library entry point once, on the sizes the benchmark uses (256^3 float32 fields,
+    128^3 for the float64 path, the imaginary-time preparation and the batch), so that one ncu
+    launch list covers every kernel of the library."""
+    import ctypes
+    import torch
+    from paper_2003_03590_gb300 import _lib
+    n = N_MAIN
+    plan = make_plan(gq, n, DT_MAIN, gq.GP_FP32)                     # default kernel variants
+    psi = init_rvr(gq, plan, seed=0)
+    plan.init_rvr(0, plan.empty(), seed=1, mode=1, count=2, p0=0.5 * math.pi, p1=math.pi)
+    plan.init_srp(0, plan.empty(), seed=2, mode=0, p0=8.0, p1=math.pi)
+    plan.init_srp(0, plan.empty(), seed=3, mode=1, p0=math.pi, p1=16)
+    plan.psi_from_phase(0, torch.zeros((n, n, n), dtype=torch.float32, device="cuda"))
+    plan.step([psi], 3)
+    plan.diagnostics(0, psi)
+    plan.structure_function(0, psi, 2)
+    plan.helicity(0, psi)
+    lam = psi.clone()
+    plan.adjoint_step(0, psi, lam, 2)
+    plan.ekin_i_grad(0, psi)
+    plan.phase_grad(0, psi, lam)
+    small = make_plan(gq, 64, DT_MAIN, gq.GP_FP32)
+    f64 = init_rvr(gq, small, seed=4)
+    a, b = small.coefficients()
+    d = _lib.Diag()
+    _lib.load().gp_diagnostics_noalloc(64, a, b, ctypes.c_void_p(f64.data_ptr()), ctypes.byref(d), None, 0,
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    p64 = make_plan(gq, 128, DT_MAIN, gq.GP_FP64)
+    g = p64.init_srp(0, p64.empty(), seed=5, mode=0, p0=4.0, p1=math.pi)
+    p64.step([g], 2)
+    p64.diagnostics(0, g)
+    prep = gq.Plan(gq.field_params(128, 0.001, alpha=0.05, beta=40.0, precision=gq.GP_FP32))
+    phi = prep.init_tg(0, prep.empty())
+    prep.argle(0, phi, gq.GP_FLOW_TG, 1.25e-2, 2)
+    prep.argle_converge(0, phi, gq.GP_FLOW_TG, 1.25e-2, 2, 0.0, check_every=2)
+    phi = prep.init_abc(0, prep.empty())
+    prep.argle(0, phi, gq.GP_FLOW_ABC, 4e-3, 2, renorm=True, energy=False)
+    sizes = [64, 64, 96, 128]
+    batch = gq.Plan([gq.field_params(m, 0.004, xi_over_dx=1.5) for m in sizes])
+    fs = [batch.init_srp(i, batch.empty(i), seed=i, mode=0, p0=4.0, p1=math.pi) for i in range(len(sizes))]
+    batch.step(fs, 2)
+    torch.cuda.synchronize()
+    for p_ in (plan, small, p64, prep, batch):
+        p_.sync()
+    return {"kernel_tour": "done", "n": n}
+
+
 def argle_leg(gq, steps=200):
     """Imaginary-time (ARGLE) preparation of the paper's 128^3 Taylor-Green run (alpha = 0.05,
     beta = 40, dtau = 1.25e-2): time per ARGLE step (five 3D transforms) in float32 and float64."""
@@ -412,6 +462,11 @@ def main():
     peak, peak_src = peaks()
     n, K, W = N_MAIN, args.steps, max(3, args.warmup)
 
+    if args.kernel_tour:
+        out = kernel_tour(gq)
+        if rank == 0:
+            print(json.dumps(out))
+        return 0
     plan = make_plan(gq, n, DT_MAIN, gq.GP_FP32)
     if args.only_diag:
         psi = init_rvr(gq, plan, seed=rank)

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "gp_internal.h"
+#include "gp_reduce.cuh"
 
 namespace gp {
 
@@ -54,37 +55,40 @@ __global__ void k_u_reg(const cpx<T>* psi, const cpx<T>* g1, const cpx<T>* g2, c
   }
 }
 
-// incompressible projection of the packed spectra, sum |u^i|^2 / 2 into acc
+// incompressible projection of the packed spectra; per-block sums of |u^i|^2 / 2 into part.
+// Per-point arithmetic in the field's precision (float64 per point is slow on GB300), sums in
+// float64 (Sums: float32 partials of at most 32 terms), added up over blocks in a fixed order.
 template <typename T>
 __global__ void k_proj_i(const cpx<T>* __restrict__ uxy, const cpx<T>* __restrict__ uz, cpx<T>* oxy, cpx<T>* oz, int n,
-                         double* acc) {
+                         double* part) {
   const long long npts = (long long)n * n * n;
-  double v = 0.0;
+  Sums<T, 1> S;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
     const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
     const long long im = ((long long)((n - iz) % n) * n + (n - iy) % n) * n + (n - ix) % n;
-    cpx<T> z = uxy[i], zm = uxy[im];
+    const cpx<T> z = uxy[i], zm = uxy[im];
     // X_k = (Z(k) + conj Z(-k)) / 2, Y_k = (Z(k) - conj Z(-k)) / (2i)
-    double xr = 0.5 * ((double)z.x + zm.x), xi = 0.5 * ((double)z.y - zm.y);
-    double yr = 0.5 * ((double)z.y + zm.y), yi = -0.5 * ((double)z.x - zm.x);
-    cpx<T> w = uz[i];
-    double zr = w.x, zi = w.y;
-    const double k0 = kwd(ix, n), k1 = kwd(iy, n), k2 = kwd(iz, n);
-    const double kk = k0 * k0 + k1 * k1 + k2 * k2;
-    if (kk > 0.0) {
-      const double cr = (k0 * xr + k1 * yr + k2 * zr) / kk, ci = (k0 * xi + k1 * yi + k2 * zi) / kk;
+    T xr = T(0.5) * (z.x + zm.x), xi = T(0.5) * (z.y - zm.y);
+    T yr = T(0.5) * (z.y + zm.y), yi = T(-0.5) * (z.x - zm.x);
+    const cpx<T> w = uz[i];
+    T zr = w.x, zi = w.y;
+    const T k0 = (T)kwd(ix, n), k1 = (T)kwd(iy, n), k2 = (T)kwd(iz, n);
+    const T kk = k0 * k0 + k1 * k1 + k2 * k2;
+    if (kk > T(0)) {
+      const T inv = T(1) / kk;
+      const T cr = (k0 * xr + k1 * yr + k2 * zr) * inv, ci = (k0 * xi + k1 * yi + k2 * zi) * inv;
       xr -= k0 * cr; xi -= k0 * ci;
       yr -= k1 * cr; yi -= k1 * ci;
       zr -= k2 * cr; zi -= k2 * ci;
     }
-    v += 0.5 * (xr * xr + xi * xi + yr * yr + yi * yi + zr * zr + zi * zi);
+    const T v[1] = {T(0.5) * (xr * xr + xi * xi + yr * yr + yi * yi + zr * zr + zi * zi)};
+    S.add(v);
     // spectrum of u^i_x + i u^i_y is X + i Y
-    oxy[i] = cpx<T>{(T)(xr - yi), (T)(xi + yr)};
-    oz[i] = cpx<T>{(T)zr, (T)zi};
+    oxy[i] = cpx<T>{xr - yi, xi + yr};
+    oz[i] = cpx<T>{zr, zi};
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(acc, v);
+  S.flush();
+  block_store<1>(S.d, part);
 }
 
 // pointwise part of lam and the fields V_j = i w_j psi whose derivatives are needed
@@ -143,10 +147,12 @@ template <typename T> static gp_status ekin_grad_impl(gp_plan* p, int field, con
   const int n = F.n;
   cudaStream_t s = p->stream;
   const size_t fb = (size_t)npts * sizeof(cpx<T>);
-  gp_status st = ensure_ws(p, field, 7 * fb);
+  const unsigned g = agrid(npts);
+  gp_status st = ensure_ws(p, field, 7 * fb + (size_t)g * sizeof(double));
   if (st != GP_OK) return st;
   cpx<T>* w[7];
   for (int i = 0; i < 7; ++i) w[i] = (cpx<T>*)F.ws + (size_t)i * npts;
+  double* part = (double*)(w[6] + npts);
   GP_CUDA(p, cudaMemcpyAsync(w[0], psi, fb, cudaMemcpyDeviceToDevice, s));
   GP_CUDA(p, fft3<T>(F, w[0], false, s));
   k_grad_spec<T><<<agrid(npts), 256, 0, s>>>(w[0], w[1], w[2], w[3], n);
@@ -154,8 +160,8 @@ template <typename T> static gp_status ekin_grad_impl(gp_plan* p, int field, con
   k_u_reg<T><<<agrid(npts), 256, 0, s>>>(psi, w[1], w[2], w[3], w[0], w[4], npts, (T)(2.0 * F.alpha), (T)eps);
   GP_CUDA(p, fft3<T>(F, w[0], false, s));
   GP_CUDA(p, fft3<T>(F, w[4], false, s));
-  GP_CUDA(p, cudaMemsetAsync(p->acc, 0, sizeof(double), s));
-  k_proj_i<T><<<agrid(npts), 256, 0, s>>>(w[0], w[4], w[5], w[6], n, p->acc);
+  k_proj_i<T><<<g, 256, 0, s>>>(w[0], w[4], w[5], w[6], n, part);
+  k_reduce<<<1, 256, 0, s>>>(part, (int)g, 1, p->acc);
   GP_CUDA(p, fft3<T>(F, w[5], true, s));
   GP_CUDA(p, fft3<T>(F, w[6], true, s));
   k_lam_local<T><<<agrid(npts), 256, 0, s>>>(psi, w[1], w[2], w[3], w[5], w[6], lam, npts, (T)eps);

@@ -35,35 +35,52 @@ struct Flow {
   double A, B, C;
 };
 
-// velocity at grid point (ix, iy, iz), x = 2 pi i / n
+// Per-axis tables of the flows' trigonometric factors (x = 2 pi i / N), formed once per call in
+// float64 with sincospi: [sin(2 pi i/N) | cos(2 pi i/N) | sin(4 pi i/N) |
+// cos(4 pi i/N)], i = 0 .. N-1, in float64 (td) and rounded to float32 (tf).  The step kernels
+// then read the velocity from them in the field's precision: GB300's float64 transcendentals
+// made the per-point evaluation the largest part of an imaginary-time step.
+__global__ void k_flow_tables(double* td, float* tf, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double inv = 2.0 / n;
+  double s1, c1, s2, c2;
+  sincospi(i * inv, &s1, &c1);
+  sincospi((double)((2 * i) % n) * inv, &s2, &c2);
+  const double v[4] = {s1, c1, s2, c2};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    td[q * n + i] = v[q];
+    tf[q * n + i] = (float)v[q];
+  }
+}
+
+// velocity at grid point (ix, iy, iz) from the tables, in the precision S of the tables
 template <typename S>
-__device__ __forceinline__ void flow_at(const Flow& f, int ix, int iy, int iz, int n, S* v) {
+__device__ __forceinline__ void flow_tab(const Flow& f, const S* __restrict__ tab, int ix, int iy, int iz, int n, S* v) {
   v[0] = v[1] = v[2] = S(0);
   if (f.kind == FLOW_NONE) return;
-  const double inv = 2.0 / n;   // sinpi/cospi take x / pi
+  const S* s1 = tab;
+  const S* c1 = tab + n;
   if (f.kind == FLOW_TG) {
-    double sx, cx, sy, cy, cz;
-    sincospi(ix * inv, &sx, &cx);
-    sincospi(iy * inv, &sy, &cy);
-    cz = cospi(iz * inv);
-    v[0] = (S)(sx * cy * cz);
-    v[1] = (S)(-cx * sy * cz);
+    const S cz = c1[iz];
+    v[0] = s1[ix] * c1[iy] * cz;
+    v[1] = -c1[ix] * s1[iy] * cz;
     return;
   }
-  double vx = 0.0, vy = 0.0, vz = 0.0;
+  const S A = (S)f.A, B = (S)f.B, C = (S)f.C;
+  S vx = S(0), vy = S(0), vz = S(0);
 #pragma unroll
-  for (int k = 1; k <= 2; ++k) {
-    double sx, cx, sy, cy, sz, cz;
-    sincospi((double)((k * ix) % n) * inv, &sx, &cx);
-    sincospi((double)((k * iy) % n) * inv, &sy, &cy);
-    sincospi((double)((k * iz) % n) * inv, &sz, &cz);
-    vx += f.B * cy + f.C * sz;
-    vy += f.C * cz + f.A * sx;
-    vz += f.A * cx + f.B * sy;
+  for (int k = 0; k < 2; ++k) {
+    const S* sk = tab + 2 * k * n;
+    const S* ck = sk + n;
+    vx += B * ck[iy] + C * sk[iz];
+    vy += C * ck[iz] + A * sk[ix];
+    vz += A * ck[ix] + B * sk[iy];
   }
-  v[0] = (S)vx;
-  v[1] = (S)vy;
-  v[2] = (S)vz;
+  v[0] = vx;
+  v[1] = vy;
+  v[2] = vz;
 }
 
 __device__ __forceinline__ int kwave(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
@@ -143,13 +160,14 @@ __global__ void k_grad_spec(const cpx<T>* ph, cpx<T>* w1, cpx<T>* w2, cpx<T>* w3
 // w1 = rest(phi, grad phi) in place of grad_x
 template <typename T>
 __global__ void k_argle_rest(const cpx<T>* __restrict__ phi, cpx<T>* w1, const cpx<T>* __restrict__ w2,
-                             const cpx<T>* __restrict__ w3, int n, Flow f, double alpha, double beta) {
+                             const cpx<T>* __restrict__ w3, int n, Flow f, const T* __restrict__ tab, double alpha,
+                             double beta) {
   const long long npts = (long long)n * n * n;
   const T q = (T)(1.0 / (4.0 * alpha)), bt = (T)beta;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
     const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
     T v[3];
-    flow_at<T>(f, ix, iy, iz, n, v);
+    flow_tab<T>(f, tab, ix, iy, iz, n, v);
     const cpx<T> p = phi[i], gx = w1[i], gy = w2[i], gz = w3[i];
     // v . grad phi
     const T dr = v[0] * gx.x + v[1] * gy.x + v[2] * gz.x;
@@ -164,12 +182,13 @@ __global__ void k_argle_rest(const cpx<T>* __restrict__ phi, cpx<T>* w1, const c
 template <typename T>
 __global__ void k_argle_combine(cpx<T>* ph, const cpx<T>* __restrict__ fr, cpx<T>* phi, int n, double dtau, double alpha) {
   const long long npts = (long long)n * n * n;
-  const double hd = 0.5 * dtau * alpha;
+  const T hd = (T)(0.5 * dtau * alpha), dt = (T)dtau;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
     const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
     const int kx = kwave(ix, n), ky = kwave(iy, n), kz = kwave(iz, n);
-    const double a = hd * (double)(kx * kx + ky * ky + kz * kz);
-    const T num = (T)(1.0 - a), den = (T)(1.0 / (1.0 + a)), dt = (T)dtau;
+    // in the field's precision (float64 division per point is slow on GB300)
+    const T a = hd * (T)(kx * kx + ky * ky + kz * kz);
+    const T num = T(1) - a, den = T(1) / (T(1) + a);
     const cpx<T> x = ph[i], r = fr[i];
     const cpx<T> y{(num * x.x + dt * r.x) * den, (num * x.y + dt * r.y) * den};
     ph[i] = y;
@@ -204,14 +223,15 @@ __global__ void k_rescale(cpx<T>* phi, cpx<T>* ph, long long npts, const double*
 // per-block sums of |grad phi - i v phi / (2 alpha)|^2 and (|phi|^2 - 1)^2
 template <typename T>
 __global__ void k_energy_v(const cpx<T>* __restrict__ phi, const cpx<T>* __restrict__ w1, const cpx<T>* __restrict__ w2,
-                           const cpx<T>* __restrict__ w3, int n, Flow f, double alpha, double* part) {
+                           const cpx<T>* __restrict__ w3, int n, Flow f, const T* __restrict__ tab, double alpha,
+                           double* part) {
   const long long npts = (long long)n * n * n;
   Sums<T, 2> S;
   const T h = (T)(1.0 / (2.0 * alpha));
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
     const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
     T v[3];
-    flow_at<T>(f, ix, iy, iz, n, v);
+    flow_tab<T>(f, tab, ix, iy, iz, n, v);
     const cpx<T> p = phi[i];
     const cpx<T> g[3] = {w1[i], w2[i], w3[i]};
     T t = 0;
@@ -286,7 +306,7 @@ static gp_status argle_impl(gp_plan* p, int field, cpx<T>* phi, Flow flow, doubl
   const size_t fb = (size_t)npts * sizeof(cpx<T>);
   const unsigned g = agrid(npts);
   const int nf = chk.every > 0 ? 5 : 4;
-  gp_status st = ensure_ws(p, field, nf * fb + (size_t)(2 * g + 16) * sizeof(double));
+  gp_status st = ensure_ws(p, field, nf * fb + (size_t)(2 * g + 16 + 4 * n) * sizeof(double) + (size_t)4 * n * sizeof(float));
   if (st != GP_OK) return st;
   cpx<T>* ph = (cpx<T>*)F.ws;
   cpx<T>* w1 = ph + npts;
@@ -297,7 +317,12 @@ static gp_status argle_impl(gp_plan* p, int field, cpx<T>* phi, Flow flow, doubl
   // red: [0] mass sum, [1] target mean |phi|^2, [2..3] energy sums, [4..5] E_v sums before and
   // [6..7] after a checked step, [8] max |phi^{n+1} - phi^n|^2
   double* red = part + 2 * g;
+  double* tab_d = red + 16;                      // flow tables, float64 and float32
+  float* tab_f = (float*)(tab_d + 4 * n);
+  const T* tab = (const T*)(sizeof(T) == 8 ? (const void*)tab_d : (const void*)tab_f);
   cudaStream_t s = p->stream;
+  k_flow_tables<<<(n + 127) / 128, 128, 0, s>>>(tab_d, tab_f, n);
+  GP_CUDA(p, cudaGetLastError());
   const double alpha = F.alpha, beta = F.beta, dn = (double)npts;
   cpx<T>* grads[3] = {w1, w2, w3};
   // E_v sums of the current phi into dst[0..1] (enqueued only; uses w1..w3)
@@ -307,7 +332,7 @@ static gp_status argle_impl(gp_plan* p, int field, cpx<T>* phi, Flow flow, doubl
     k_grad_spec<T><<<g, 256, 0, s>>>(w1, w1, w2, w3, n);   // in place: w1 is read before it is written
     GP_CUDA(p, cudaGetLastError());
     GP_CUDA(p, transform<T>(p, F, grads, 3, true, s));
-    k_energy_v<T><<<g, 256, 0, s>>>(phi, w1, w2, w3, n, flow, alpha, part);
+    k_energy_v<T><<<g, 256, 0, s>>>(phi, w1, w2, w3, n, flow, tab, alpha, part);
     k_reduce<<<1, 256, 0, s>>>(part, (int)g, 2, dst);
     GP_CUDA(p, cudaGetLastError());
     return GP_OK;
@@ -336,7 +361,7 @@ static gp_status argle_impl(gp_plan* p, int field, cpx<T>* phi, Flow flow, doubl
       k_grad_spec<T><<<g, 256, 0, s>>>(ph, w1, w2, w3, n);
       GP_CUDA(p, cudaGetLastError());
       GP_CUDA(p, transform<T>(p, F, grads, 3, true, s));
-      k_argle_rest<T><<<g, 256, 0, s>>>(phi, w1, w2, w3, n, flow, alpha, beta);
+      k_argle_rest<T><<<g, 256, 0, s>>>(phi, w1, w2, w3, n, flow, tab, alpha, beta);
       GP_CUDA(p, cudaGetLastError());
       GP_CUDA(p, transform<T>(p, F, &w1, 1, false, s));
       k_argle_combine<T><<<g, 256, 0, s>>>(ph, w1, phi, n, dtau, alpha);

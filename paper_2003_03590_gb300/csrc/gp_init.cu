@@ -79,21 +79,39 @@ template <typename T> __global__ void k_copy_out(const double2* w, cpx<T>* psi, 
 // ---------------------------------------------------------------- SRP, spline
 // theta(x, y, z) = sum_{k,j,i} S[z][k] S[y][j] S[x][i] lat[k][j][i] with S the N x N_r matrix of
 // the periodic cubic spline (the paper's sequential x, y, z interpolation is this tensor product).
+// The interpolation is separable: theta(ix, iy, iz) = sum_k S[iz][k] sum_j S[iy][j] sum_q S[ix][q]
+// lat[k][j][q].  The two inner sums are formed once on their own grids (nr^2 x N, then nr x N^2
+// values) and every point only does the outer one; each sum runs over the same terms in the same
+// order as written, so the values are those of the direct triple sum.
+__global__ void k_spline_x(const double* __restrict__ S, const double* __restrict__ lat, int n, int nr, double* T1) {
+  const long long total = (long long)nr * nr * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % n);
+    const long long kj = i / n;                     // k nr + j
+    double tx = 0.0;
+    for (int q = 0; q < nr; ++q) tx += S[(long long)ix * nr + q] * lat[kj * nr + q];
+    T1[i] = tx;                                     // [k][j][ix]
+  }
+}
+__global__ void k_spline_y(const double* __restrict__ S, const double* __restrict__ T1, int n, int nr, double* T2) {
+  const long long total = (long long)nr * n * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % n);
+    const int iy = (int)((i / n) % n);
+    const int k = (int)(i / ((long long)n * n));
+    double ty = 0.0;
+    for (int j = 0; j < nr; ++j) ty += S[(long long)iy * nr + j] * T1[((long long)k * nr + j) * n + ix];
+    T2[i] = ty;                                     // [k][iy][ix]
+  }
+}
 template <typename T>
-__global__ void k_spline(const double* __restrict__ S, const double* __restrict__ lat, int n, int nr, cpx<T>* psi) {
-  const long long npts = (long long)n * n * n;
+__global__ void k_spline(const double* __restrict__ S, const double* __restrict__ T2, int n, int nr, cpx<T>* psi) {
+  const long long npts = (long long)n * n * n, nn = (long long)n * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
+    const long long iyx = i % nn;
+    const int iz = (int)(i / nn);
     double th = 0.0;
-    for (int k = 0; k < nr; ++k) {
-      double ty = 0.0;
-      for (int j = 0; j < nr; ++j) {
-        double tx = 0.0;
-        for (int q = 0; q < nr; ++q) tx += S[(long long)ix * nr + q] * lat[((long long)k * nr + j) * nr + q];
-        ty += S[(long long)iy * nr + j] * tx;
-      }
-      th += S[(long long)iz * nr + k] * ty;
-    }
+    for (int k = 0; k < nr; ++k) th += S[(long long)iz * nr + k] * T2[(long long)k * nn + iyx];
     double sn, cs;
     sincos(th, &sn, &cs);
     psi[i] = cpx<T>{(T)cs, (T)sn};
@@ -189,11 +207,13 @@ __global__ void k_rings(const Ring* __restrict__ rings, int count, int n, double
       const double p0 = d0 - zp * g.nx, p1 = d1 - zp * g.ny, p2 = d2 - zp * g.nz;
       const double rp = sqrt(p0 * p0 + p1 * p1 + p2 * p2);
       const double s = sqrt((rp - g.R) * (rp - g.R) + zp * zp);
-      const double f = tanh(s * inv);
-      const double ph = atan2(zp, rp - g.R);
-      double sn, cs;
-      sincos(ph, &sn, &cs);
-      const double fr = f * cs, fi = f * sn;
+      // tanh(s / (sqrt 2 xi)) exp(i atan2(z', rho' - R)) = tanh(.) (rho' - R + i z') / s: the
+      // phase factor is the unit vector of the core offset (no float64 atan2 and sincos, which
+      // are slow on GB300); at s = 0 the amplitude is 0
+      // (beyond 22 core widths tanh is 1 to far below an ulp: skip the float64 tanh there)
+      const double sa = s * inv;
+      const double f = s > 0.0 ? (sa < 22.0 ? tanh(sa) : 1.0) / s : 0.0;
+      const double fr = f * (rp - g.R), fi = f * zp;
       const double nr = re * fr - im * fi, ni = re * fi + im * fr;
       re = nr;
       im = ni;
@@ -211,9 +231,9 @@ __device__ __forceinline__ double2 vring(double x, double y, double z, double R,
   const double d = sqrt((r - R) * (r - R) + zt * zt);
   const double e2 = (d / xi) * (d / xi);
   const double f = sqrt((a1 * e2 + a2 * e2 * e2) / (1.0 + b1 * e2 + a2 * e2 * e2));
-  double sn, cs;
-  sincos(atan2(zt, r - R), &sn, &cs);
-  return make_double2(f * cs, f * sn);
+  // f exp(i atan2(z~, r - R)) = f (r - R + i z~) / d (the amplitude vanishes at d = 0)
+  const double q = d > 0.0 ? f / d : 0.0;
+  return make_double2(q * (r - R), q * zt);
 }
 __device__ __forceinline__ double2 dmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -299,14 +319,19 @@ template <typename T> static gp_status srp_spline(gp_plan* p, int field, cpx<T>*
   std::vector<double> S = spline_matrix(n, nr);
   std::vector<double> lat((size_t)nr * nr * nr);
   for (size_t i = 0; i < lat.size(); ++i) lat[i] = K * (2.0 * u01(splitmix_at(stream_pos(seed, i))) - 1.0);
-  gp_status st = ensure_ws(p, field, (S.size() + lat.size()) * sizeof(double));
+  const size_t t1 = (size_t)nr * nr * n, t2 = (size_t)nr * n * n;
+  gp_status st = ensure_ws(p, field, (S.size() + lat.size() + t1 + t2) * sizeof(double));
   if (st != GP_OK) return st;
   double* dS = (double*)F.ws;
   double* dL = dS + S.size();
+  double* dT1 = dL + lat.size();
+  double* dT2 = dT1 + t1;
   cudaStream_t s = p->stream;
   GP_CUDA(p, cudaMemcpyAsync(dS, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   GP_CUDA(p, cudaMemcpyAsync(dL, lat.data(), lat.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  k_spline<T><<<igrid(F.npts), 256, 0, s>>>(dS, dL, n, nr, psi);
+  k_spline_x<<<igrid((long long)t1), 256, 0, s>>>(dS, dL, n, nr, dT1);
+  k_spline_y<<<igrid((long long)t2), 256, 0, s>>>(dS, dT1, n, nr, dT2);
+  k_spline<T><<<igrid(F.npts), 256, 0, s>>>(dS, dT2, n, nr, psi);
   GP_CUDA(p, cudaGetLastError());
   GP_CUDA(p, cudaStreamSynchronize(s));  // host vectors go out of scope
   return GP_OK;
