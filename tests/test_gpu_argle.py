@@ -131,7 +131,7 @@ def test_tg_preparation_reproduces_the_paper_table(prec):
     1e-4, the small compressible part (4.9e-4 of an energy of 0.15, the most sensitive to how far
     the flow has converged) to 5e-3, the mass to 1e-6."""
     n = 128
-    plan = _plan(n, prec)
+    plan = Plan(field_params(n, 1.25e-3, alpha=0.05, beta=40.0, precision=prec))   # TG_a's real-time dt
     psi = plan.init_tg(0, plan.empty())
     ev = plan.argle(0, psi, GP_FLOW_TG, 1.25e-2, 4800)
     d, _ = plan.diagnostics(0, psi)
@@ -148,6 +148,42 @@ def test_tg_preparation_reproduces_the_paper_table(prec):
     h, _ = plan.helicity(0, psi, spectra=False)
     print(h)
     assert abs(h["H"]) < 1e-5 and abs(h["H_reg"]) < 1e-5
+    _real_time_conservation(plan, psi, d, steps=9600, every=100, paper_n=0.9789997, paper_e_end=0.1504111,
+                            paper_delta_e=7.97e-5, prec=prec, tol=1e-4)
+
+
+def _real_time_conservation(plan, psi, d0, steps, every, paper_n, paper_e_end, paper_delta_e, prec, tol):
+    """The paper's real-time run from the prepared field (its conservation table: N at t = 0 and
+    T_f, E at t = 0 and T_f, delta(E) = max_t |E(t) - E(0)| / E(0)), with the fused split step:
+    N is conserved to the rounding of the step (the scheme conserves it exactly), the final
+    energy agrees with the printed one to the accuracy of the prepared field (tol: that of the
+    energies above), and delta(E) -- the splitting error of a second-order scheme at the
+    paper's dt over its whole run -- has the printed magnitude (within a factor 2: the paper
+    prints the order KNK of its Strang step, the library's default order is NKN).  Measured,
+    float64: TG_a E(T_f) = 0.15041109 (printed 0.1504111), ABC_a delta(E) 6.07e-5 (5.98e-5)."""
+    e0, n0 = d0["E"], d0["N"]
+    dev = 0.0
+    for _ in range(steps // every):
+        plan.step([psi], every)
+        d, _ = plan.diagnostics(0, psi, spectra=False)
+        dev = max(dev, abs(d["E"] - e0) / e0)
+    print({"N_end": d["N"], "N_drift": d["N"] / n0 - 1, "E_end": d["E"], "paper_E_end": paper_e_end,
+           "delta_E": dev, "paper_delta_E": paper_delta_e})
+    # Rounding only (the scheme conserves N exactly).  float64: ~3e-16 per step.  float32: on
+    # these fields, whose mass sits almost wholly in the k = 0 mode, the rounding of the
+    # transforms does not average out and N drifts by 4e-9..8e-9 per step (measured 7.2e-5 over
+    # TG_a's 9600 steps, 25 times less than a float32 FFT with float32 twiddles gives on such a
+    # field): above the 1e-6 per 1000 steps aimed at, which the float32 path meets on the random
+    # and ring fields of the step tests but not here -- see the design notes.
+    assert abs(d["N"] / n0 - 1) < (1e-4 if prec == GP_FP32 else 1e-10)
+    assert d["N"] == pytest.approx(paper_n, rel=tol)
+    assert d["E"] == pytest.approx(paper_e_end, rel=tol)
+    # the splitting error itself: float64 within a factor 2 of the printed delta(E) (measured
+    # 7.05e-5 against 7.97e-5 for TG_a, 6.07e-5 against 5.98e-5 for ABC_a); float32 below twice
+    # it (its mass drift above moves E as well: 3.3e-5 for TG_a)
+    assert dev < 2.0 * paper_delta_e
+    if prec == GP_FP64:
+        assert dev > 0.5 * paper_delta_e
 
 
 @pytest.mark.parametrize("prec", [GP_FP64, GP_FP32])
@@ -158,7 +194,7 @@ def test_abc_preparation_against_the_paper_table(prec):
     E_int = 0.0430379, H_reg = 2.4726091; (ABC conservation table, t = 0): N = 0.9410138,
     E = 1.0206996."""
     n = 128
-    plan = _plan(n, prec)
+    plan = Plan(field_params(n, 8e-4, alpha=0.05, beta=40.0, precision=prec))       # ABC_a's real-time dt
     psi = plan.init_abc(0, plan.empty())
     plan.argle(0, psi, GP_FLOW_ABC, 4e-3, 7500, energy=False)
     d, _ = plan.diagnostics(0, psi)
@@ -173,3 +209,5 @@ def test_abc_preparation_against_the_paper_table(prec):
     h, spec = plan.helicity(0, psi)
     print(h, spec["H_reg"][:6])
     assert h["H_reg"] == pytest.approx(2.4726091, rel=2e-2)
+    _real_time_conservation(plan, psi, d, steps=12500, every=125, paper_n=0.9410138, paper_e_end=1.0206400,
+                            paper_delta_e=5.98e-5, prec=prec, tol=2e-2)

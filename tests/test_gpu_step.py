@@ -115,17 +115,21 @@ def test_fp32_mass_drift_over_1000_steps(n, bound):
 
 @pytest.mark.parametrize("n", [32, 48, 64, 96, 128, 192])
 def test_fp32_transforms_have_no_mass_bias(n):
-    """With alpha = beta ~ 0 a step is a forward and an inverse 3D FFT (and the 1/N^3): on a
-    random field whose mass is spread over all modes the float32 round trips must not change the
-    mass systematically.  A fixed rounding bias (a float-rounded twiddle, or a compensation term
-    lost in an exact product, as radix-3 lengths once had) shows up as a linear drift of
-    ~1e-6 per 1000 steps; unbiased round-off stays near 1e-8."""
-    plan = Plan(field_params(n, 0.002, alpha=1e-300, beta=1e-300))
+    """The float32 transforms and kinetic factor must not change the mass systematically.  With
+    beta ~ 0 a step is a forward 3D FFT, the kinetic factor and an inverse FFT; alpha must be
+    non-zero: without the kinetic factor the round trip reaches a fixed point of its own rounding
+    after a step or two and no drift can show.  On a random field whose mass is spread over all
+    modes the unbiased (hi + lo) twiddles and factors keep the drift at the level of the rounding
+    random walk (measured <= ~5e-7 over 1000 steps); a float-rounded twiddle or a lost
+    compensation term (as radix-3 lengths once had) drifts ~1e-5..1e-4 over the same steps, as a
+    float32 FFT with float32 twiddles does."""
+    plan = Plan(field_params(n, 0.002, alpha=0.05, beta=1e-300))
     psi = to_gpu(random_psi(n, 1, amp_jitter=0.1), np.complex64)
     m0 = plan.diagnostics(0, psi, spectra=False)[0]["N"]
     plan.step([psi], 1000)
     m = plan.diagnostics(0, psi, spectra=False)[0]["N"]
-    assert abs(m - m0) / m0 < 1.5e-7
+    print(n, m / m0 - 1)
+    assert abs(m - m0) / m0 < 2e-6
 
 
 @pytest.mark.parametrize("n", [128, 256])
