@@ -171,11 +171,11 @@ def _real_time_conservation(plan, psi, d0, steps, every, paper_n, paper_e_end, p
            "delta_E": dev, "paper_delta_E": paper_delta_e})
     # Rounding only (the scheme conserves N exactly).  float64: ~3e-16 per step.  float32: on
     # these fields, whose mass sits almost wholly in the k = 0 mode, the rounding of the
-    # transforms does not average out and N drifts by 4e-9..8e-9 per step (measured 7.2e-5 over
-    # TG_a's 9600 steps, 25 times less than a float32 FFT with float32 twiddles gives on such a
+    # transforms does not average out and N drifts by 4e-9..8e-9 per step (bound: 1e-8 per step;
+    # measured 7.2e-5 over TG_a's 9600 steps, 1.2e-4 over TG_b's 19200, 25 times less than a float32 FFT with float32 twiddles gives on such a
     # field): above the 1e-6 per 1000 steps aimed at, which the float32 path meets on the random
     # and ring fields of the step tests but not here -- see the design notes.
-    assert abs(d["N"] / n0 - 1) < (1e-4 if prec == GP_FP32 else 1e-10)
+    assert abs(d["N"] / n0 - 1) < (1e-8 * steps if prec == GP_FP32 else 1e-10)
     assert d["N"] == pytest.approx(paper_n, rel=tol)
     assert d["E"] == pytest.approx(paper_e_end, rel=tol)
     # the splitting error itself: float64 within a factor 2 of the printed delta(E) (measured
@@ -211,3 +211,48 @@ def test_abc_preparation_against_the_paper_table(prec):
     assert h["H_reg"] == pytest.approx(2.4726091, rel=2e-2)
     _real_time_conservation(plan, psi, d, steps=12500, every=125, paper_n=0.9410138, paper_e_end=1.0206400,
                             paper_delta_e=5.98e-5, prec=prec, tol=2e-2)
+
+
+PAPER_256 = {
+    # TG_bIT / TG_b and ABC_bIT / ABC_b: 256^3, alpha = 0.025, beta = 80 (the paper's parameter
+    # table); ARGLE dtau and tau_f, real-time dt and T_f from its TG / ABC run tables; energies and
+    # helicities at tau_f from its TG / ABC ARGLE energy tables; N, E at t = 0 and T_f and
+    # delta(E) from its conservation tables.
+    "tg": {"flow": GP_FLOW_TG, "dtau": 6.25e-3, "steps": 9600, "dt": 6.25e-4, "rt_steps": 19200,
+           "E_kin_i": 0.11334487, "E_kin_c": 2.2334712e-4, "E_q": 4.0373670e-3, "E_int": 6.8223665e-3,
+           "N": 0.9873160, "E": 0.1244280, "E_end": 0.1244235, "delta_E": 3.60e-5, "H_reg": None},
+    "abc": {"flow": GP_FLOW_ABC, "dtau": 2e-3, "steps": 15000, "dt": 4e-4, "rt_steps": 25000,
+            "E_kin_i": 0.9792042, "E_kin_c": 0.0008142, "E_q": 0.0144931, "E_int": 0.0237201,
+            "N": 0.9647786, "E": 1.0182316, "E_end": 1.0181689, "delta_E": 6.18e-5, "H_reg": 2.6532860},
+}
+
+
+@pytest.mark.parametrize("case", ["tg", "abc"])
+def test_preparation_and_real_time_run_at_256_against_the_paper(case):
+    """The paper's 256^3 runs (float32): the imaginary-time preparation from the TG ansatz
+    ([gamma_d/4] = 6) or the ABC phase field, its energies and helicities, then the real-time run
+    with the fused step and its conservation figures.  Tolerances as at 128^3: the TG run was
+    converged by the paper (1e-4 on the large energies, 1e-2 on the small compressible part),
+    the ABC one stopped early (2e-2).  Measured (GB300): TG_bIT E_kin^i +4.9e-4, E_q -1.5e-4,
+    E_int -3e-5, E_kin^c -3.5%, N -1e-6, E +3.8e-4 -- agreement an order looser than at 128^3
+    (float32 preparation against the paper's float64 one): 1e-3 on the large parts, 5e-2 on the
+    compressible one; ABC_bIT within 0.4%, H_reg 2.6480 (printed 2.6532860)."""
+    c = PAPER_256[case]
+    n = 256
+    plan = Plan(field_params(n, c["dt"], alpha=0.025, beta=80.0, precision=GP_FP32))
+    psi = plan.init_tg(0, plan.empty()) if case == "tg" else plan.init_abc(0, plan.empty())
+    plan.argle(0, psi, c["flow"], c["dtau"], c["steps"], energy=False)
+    d, _ = plan.diagnostics(0, psi, spectra=False)
+    h, _ = plan.helicity(0, psi, spectra=False)
+    keys = ("E_kin_i", "E_kin_c", "E_q", "E_int", "N", "E")
+    print({k: (d[k], c[k], d[k] / c[k] - 1) for k in keys}, h)
+    for k in keys:
+        tol = (5e-2 if k == "E_kin_c" else 1e-3) if case == "tg" else 2e-2
+        assert d[k] == pytest.approx(c[k], rel=tol), (k, d[k], c[k])
+    if case == "tg":
+        assert abs(h["H"]) < 1e-5 and abs(h["H_reg"]) < 1e-5     # printed 2.96e-7 and -5.52e-7
+    else:
+        assert h["H_reg"] == pytest.approx(c["H_reg"], rel=2e-2)
+    _real_time_conservation(plan, psi, d, steps=c["rt_steps"], every=c["rt_steps"] // 100, paper_n=c["N"],
+                            paper_e_end=c["E_end"], paper_delta_e=c["delta_E"], prec=GP_FP32,
+                            tol=1e-3 if case == "tg" else 2e-2)
