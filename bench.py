@@ -50,6 +50,9 @@ def parse():
                     help="init, then CALLS diagnostics calls of the step workload's field (profiling)")
     ap.add_argument("--kernel-tour", action="store_true",
                     help="every library entry point once on the benchmark's sizes, then exit (for a per-kernel ncu list)")
+    ap.add_argument("--paper-prep", default=None, metavar="CASE",
+                    help="one of the paper's imaginary-time preparations (tg_a..tg_d, abc_a..abc_c): our energies, "
+                         "helicities and Mach numbers next to the printed ones, then exit")
     ap.add_argument("--tune-cache", default=None,
                     help="JSON file of kernel choices: read if present (no tuning launches), else written")
     return ap.parse_args()
@@ -347,6 +350,58 @@ def analysis_leg(plan, psi, calls=3):
     return out
 
 
+# The paper's preparations: its parameter table (alpha, beta per resolution), its TG / ABC run
+# tables (dtau, tau_f) and, at tau_f, its ARGLE energy tables (E_kin^i, E_kin^c, E_q, E_int, H,
+# H_reg), its conservation tables (N, E at t = 0) and its ABC Mach table (ABC_c only).
+PAPER_PREP = {
+    "tg_a": (128, 0.05, 40.0, "tg", 1.25e-2, 60, dict(E_kin_i=0.12901707, E_kin_c=4.8667051e-4, E_q=7.9239425e-3,
+                                                      E_int=1.2995235e-2, H=1.37e-13, H_reg=-1.87e-11, N=0.9789997,
+                                                      E=0.1504230)),
+    "tg_b": (256, 0.025, 80.0, "tg", 6.25e-3, 60, dict(E_kin_i=0.11334487, E_kin_c=2.2334712e-4, E_q=4.0373670e-3,
+                                                       E_int=6.8223665e-3, H=2.96e-7, H_reg=-5.52e-7, N=0.9873160,
+                                                       E=0.1244280)),
+    "tg_c": (512, 0.0125, 160.0, "tg", 3.125e-3, 60, dict(E_kin_i=0.12884207, E_kin_c=1.5065059e-4, E_q=2.4895687e-3,
+                                                          E_int=4.2864757e-3, H=3.83e-3, H_reg=-5.63e-7, N=0.9920083,
+                                                          E=0.1357688)),
+    "tg_d": (1024, 0.00625, 320.0, "tg", 1.5625e-3, 60, dict(E_kin_i=0.12968555, E_kin_c=9.5590716e-5, E_q=1.3476259e-3,
+                                                             E_int=2.3466209e-3, H=-3.94e-4, H_reg=-9.71e-8, N=0.9955732,
+                                                             E=0.1275738)),
+    "abc_a": (128, 0.05, 40.0, "abc", 4e-3, 30, dict(E_kin_i=0.9485114, E_kin_c=0.0014218, E_q=0.0277287,
+                                                    E_int=0.0430379, H=2.4106982, H_reg=2.4726091, N=0.9410138,
+                                                    E=1.0206996)),
+    "abc_b": (256, 0.025, 80.0, "abc", 2e-3, 30, dict(E_kin_i=0.9792042, E_kin_c=0.0008142, E_q=0.0144931,
+                                                     E_int=0.0237201, H=2.7439625, H_reg=2.6532860, N=0.9647786,
+                                                     E=1.0182316)),
+    "abc_c": (512, 0.0125, 160.0, "abc", 1e-3, 30, dict(E_kin_i=0.9884992, E_kin_c=0.0006486, E_q=0.0073802,
+                                                       E_int=0.0124975, H=2.7217161, H_reg=2.7365301, N=0.9796053,
+                                                       E=1.0090255, M_max=1.486860, M_rms=0.703259)),
+}
+
+
+def paper_prep(gq, case):
+    """One of the paper's imaginary-time preparations with its parameters (float32 field), then the
+    diagnostics (with the Mach numbers) and both helicities of the prepared field, each next to the
+    value the paper prints and their relative difference."""
+    import torch
+    n, alpha, beta, kind, dtau, tau_f, paper = PAPER_PREP[case]
+    plan = gq.Plan(gq.field_params(n, 1e-3, alpha=alpha, beta=beta, precision=gq.GP_FP32))
+    psi = plan.init_tg(0, plan.empty()) if kind == "tg" else plan.init_abc(0, plan.empty())
+    steps = int(round(tau_f / dtau))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.argle(0, psi, gq.GP_FLOW_TG if kind == "tg" else gq.GP_FLOW_ABC, dtau, steps, energy=False)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    d, _ = plan.diagnostics(0, psi, spectra=False)
+    h, _ = plan.helicity(0, psi, spectra=False)
+    got = dict(d)
+    got.update(h)
+    rows = {k: {"ours": got[k], "paper": v, "rel": (got[k] / v - 1) if abs(v) > 1e-6 else None}
+            for k, v in paper.items()}
+    return {"paper_prep": case, "n": n, "alpha": alpha, "beta": beta, "dtau": dtau, "argle_steps": steps,
+            "argle_seconds": secs, "precision": "f32", "values": rows}
+
+
 def kernel_tour(gq):
     """Every library entry point once, on the sizes the benchmark uses (256^3 float32 fields,
     128^3 for the float64 path, the imaginary-time preparation and the batch), so that one ncu
@@ -462,6 +517,11 @@ def main():
     peak, peak_src = peaks()
     n, K, W = N_MAIN, args.steps, max(3, args.warmup)
 
+    if args.paper_prep:
+        out = paper_prep(gq, args.paper_prep)
+        if rank == 0:
+            print(json.dumps(out))
+        return 0
     if args.kernel_tour:
         out = kernel_tour(gq)
         if rank == 0:
