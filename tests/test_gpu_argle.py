@@ -256,3 +256,23 @@ def test_preparation_and_real_time_run_at_256_against_the_paper(case):
     _real_time_conservation(plan, psi, d, steps=c["rt_steps"], every=c["rt_steps"] // 100, paper_n=c["N"],
                             paper_e_end=c["E_end"], paper_delta_e=c["delta_E"], prec=GP_FP32,
                             tol=1e-3 if case == "tg" else 2e-2)
+
+
+def test_tg_grid_convergence_case_h_against_the_paper():
+    """The paper's grid-convergence run TG_h: the TG_a preparation (alpha = 0.05, beta = 40) on
+    256^3 (dx/xi = 0.694), against its grid-energy table (six digits; E_v compared as E_v / (2 alpha),
+    as for TG_a).  The table gives no dtau for it: read as the dtau of the paper's 256^3 TG run
+    (TG_bIT: 6.25e-3, tau_f = 60, 9600 steps) -- with TG_a's 1.25e-2 the explicit advection is
+    unstable at 256^3 (|v| k_max dtau = 1.6) and the flow blows up.  (TG_g, 64^3 with
+    dx/xi = 2.776, is not pinned: under-resolved, the flow ends in a different local minimum of
+    E_v in float32 and in float64 -- E_kin^i 0.1264 and 0.1174 against the printed 0.1299.)"""
+    paper = {"E_kin_i": 1.29562e-1, "E_kin_c": 2.72478e-4, "E_q": 7.80383e-3, "E_int": 1.30274e-2, "E_v": 7.10095e-1}
+    plan = Plan(field_params(256, 1.25e-3, alpha=0.05, beta=40.0, precision=GP_FP32))
+    psi = plan.init_tg(0, plan.empty())
+    ev = plan.argle(0, psi, GP_FLOW_TG, 6.25e-3, 9600)
+    d, _ = plan.diagnostics(0, psi, spectra=False)
+    got = {k: d[k] for k in ("E_kin_i", "E_kin_c", "E_q", "E_int")}
+    got["E_v"] = ev / (2 * 0.05)
+    print({k: (got[k], paper[k], got[k] / paper[k] - 1) for k in paper})
+    for k in paper:
+        assert got[k] == pytest.approx(paper[k], rel=5e-3 if k == "E_kin_c" else 1e-4), (k, got[k], paper[k])
