@@ -163,7 +163,7 @@ __device__ __forceinline__ void sweep_op_body(const SweepArgs<T>& a, int t, int 
       // every step
       const float4 eo = __ldg(a.ek2 + i2 * L + i1);
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = twmul(twmul(v[e], __ldg(a.ekx + out_pos<L, false>(e, t))), eo);
+      for (int e = 0; e < E; ++e) v[e] = twmul_k(twmul_k(v[e], __ldg(a.ekx + out_pos<L, false>(e, t))), eo);
     } else {
       const V eo = cmul(__ldg(a.ek + i1), __ldg(a.ek + i2));
 #pragma unroll
