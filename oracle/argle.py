@@ -13,7 +13,7 @@ Laplacian implicit, everything else explicit at the old level,
 solved exactly in Fourier space (the implicit part is diagonal):
     F phi' = [ (1 - dtau alpha |k|^2 / 2) F phi + dtau F(rest) ] / (1 + dtau alpha |k|^2 / 2),
     rest = -i v . grad phi - |v|^2/(4 alpha) phi + beta (1 - |phi|^2) phi.
-Readings (each listed in the design notes): the printed right-hand side applies the explicit
+Readings: the printed right-hand side applies the explicit
 operator to "phi~^n", read as phi^n (the old level); first derivatives use Nyquist-zeroed
 wavenumbers, the Laplacian the full |k|^2; the optional L2 renormalisation (the normalised
 gradient flow the section starts from) rescales phi after each step to a prescribed mean

@@ -12,7 +12,7 @@ Momentum <rho v> = 2 alpha <Im(psi* grad psi)> (eq-mom-total, eq-scaling-rhov) a
 numbers of sqrt(rho) v (eq:Mach-Number): M_max = max |sqrt(rho) v| / c, M_rms = sqrt(2 E_kin) / c,
 with the sound speed c = sqrt(2 alpha beta) (c^2 / 2 is the coefficient of (rho - 1)^2 in E).
 
-Readings where the paper is silent (each listed in the design notes):
+Readings where the paper is silent:
   * first derivatives use i k~ with the Nyquist component of k~ set to zero;
     the gradient energy in E uses the Laplacian-consistent |k|^2 (Nyquist kept);
   * sqrt(rho) v and grad sqrt(rho) use u = 2 alpha Im(psi* grad psi)/|psi| and

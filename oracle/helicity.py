@@ -15,7 +15,7 @@ Helicity spectra: H(k) and H_reg(k) are the shell sums (shell floor(|k| + 1/2)) 
 Re(conj(F v) . F omega) / n^2 and Re(conj(F v_reg) . F omega) / n^2, so that they add up to
 H and H_reg (Parseval with the unnormalised DFT F and n grid points).
 
-Readings where the paper is silent (each listed in the design notes):
+Readings where the paper is silent:
   * v is the velocity of the structure functions and diagnostics: 2 alpha Im(psi* grad psi) /
     |psi|^2, 0 where |psi|^2 < 1e-12; omega is its spectral curl (i k~ x F v, the
     Nyquist-zeroed wavenumbers of every first derivative);

@@ -8,7 +8,7 @@ strfunc-def (Sec. 3.5): along the unit vector e_j,
 a volume mean over the grid, for separations r = s dx, dx = 2 pi / N, s = 0 .. N/2 (on the
 periodic grid S^p_j(N dx - r) = (-1)^p S^p_j(r), so those shifts carry all of it).
 
-Readings where the paper is silent (each listed in the design notes):
+Readings where the paper is silent:
   * v is the superfluid velocity of eq-scaling-rhov, v = 2 alpha Im(psi* grad psi) / |psi|^2,
     with the spectral gradient of the other diagnostics (Nyquist-zeroed wavenumbers) and v = 0
     where |psi|^2 < eps_rho = 1e-12 (the same cut as sqrt(rho) v);

@@ -1,5 +1,5 @@
 """The float32 arithmetic fact behind the kinetic factor's product order (twmul_k in the CUDA
-source; see the precision notes of the design): a compensated complex product a * (c + i s),
+source): a compensated complex product a * (c + i s),
 applied again and again by the same small angle, gains |a|^2 steadily when a component's small
 terms are first summed against its larger product alone and rounded there, and does not when the
 larger product is added last.  Pure numpy emulation of float32 FMA (the exact product of two

@@ -174,7 +174,7 @@ def _real_time_conservation(plan, psi, d0, steps, every, paper_n, paper_e_end, p
     # transforms does not average out and N drifts by 4e-9..8e-9 per step (bound: 1e-8 per step;
     # measured 7.2e-5 over TG_a's 9600 steps, 1.2e-4 over TG_b's 19200, 25 times less than a float32 FFT with float32 twiddles gives on such a
     # field): above the 1e-6 per 1000 steps aimed at, which the float32 path meets on the random
-    # and ring fields of the step tests but not here -- see the design notes.
+    # and ring fields of the step tests but not here.
     assert abs(d["N"] / n0 - 1) < (1e-8 * steps if prec == GP_FP32 else 1e-10)
     assert d["N"] == pytest.approx(paper_n, rel=tol)
     assert d["E"] == pytest.approx(paper_e_end, rel=tol)
