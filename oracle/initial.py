@@ -187,7 +187,21 @@ def vortex_ring_pair_periodised(x, y, z, R, d, xi):
 AXIS_ORDERS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
 
 
-def rvr_pade(n, seed, xi, npairs, R=0.5 * math.pi, d=math.pi):
+def rvr_pade_draws(seed, npairs):
+    """The random part of rvr_pade: per pair a translation X = 2 pi (u0, u1, u2) and an axis order
+    index floor(6 u3), pair p using stream positions 4p .. 4p+3."""
+    shifts, orders = [], []
+    for pidx in range(npairs):
+        u = [float(rng.uniform01(rng.splitmix64(rng.positions(seed, 4 * pidx + c)))) for c in range(4)]
+        shifts.append((2.0 * math.pi * u[0], 2.0 * math.pi * u[1], 2.0 * math.pi * u[2]))
+        orders.append(min(int(6.0 * u[3]), 5))
+    return shifts, orders
+
+
+def rvr_pade_from(n, xi, shifts, orders, R=0.5 * math.pi, d=math.pi):
+    """Product over pairs p of the periodised pair translated by shifts[p] = (X, Y, Z) (spectral
+    shift with the Nyquist-zeroed wavenumbers: moved(x) = base(x + X)) and read in the axis order
+    AXIS_ORDERS[orders[p]] = s: the factor at the point (x0, x1, x2) is moved(x_s0, x_s1, x_s2)."""
     pts = grid_points(n)
     base = vortex_ring_pair_periodised(pts[..., 0], pts[..., 1], pts[..., 2], R, d, xi)
     bh = fft.fft3(base)
@@ -196,12 +210,15 @@ def rvr_pade(n, seed, xi, npairs, R=0.5 * math.pi, d=math.pi):
     I = np.meshgrid(idx, idx, idx, indexing="ij")          # [iz, iy, ix]
     coords = (I[2], I[1], I[0])                            # (x index, y index, z index)
     psi = np.ones((n, n, n), dtype=np.complex128)
-    for pidx in range(npairs):
-        u = [float(rng.uniform01(rng.splitmix64(rng.positions(seed, 4 * pidx + c)))) for c in range(4)]
-        X = [2.0 * math.pi * u[0], 2.0 * math.pi * u[1], 2.0 * math.pi * u[2]]
+    for X, o in zip(shifts, orders):
         shift = np.exp(1j * (kd[None, None, :] * X[0] + kd[None, :, None] * X[1] + kd[:, None, None] * X[2]))
         moved = fft.ifft3(shift * bh)                      # moved(x) = base(x + X)
-        order = AXIS_ORDERS[min(int(6.0 * u[3]), 5)]
+        order = AXIS_ORDERS[o]
         a = [coords[order[0]], coords[order[1]], coords[order[2]]]
         psi *= moved[a[2], a[1], a[0]]                     # value of moved at (a0, a1, a2)
     return psi
+
+
+def rvr_pade(n, seed, xi, npairs, R=0.5 * math.pi, d=math.pi):
+    shifts, orders = rvr_pade_draws(seed, npairs)
+    return rvr_pade_from(n, xi, shifts, orders, R, d)

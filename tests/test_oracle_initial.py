@@ -155,3 +155,101 @@ def test_rvr_pade_building_blocks():
     psi = I.rvr_pade(n, 5, xi, 2)
     assert psi.shape == (n, n, n) and np.isfinite(psi).all()
     assert np.max(np.abs(psi)) < 1.05
+
+
+# ---- the composite of the paper's ring-pair field (Sec. 5.4: eq-one-vortex-ring, eq-Pade,
+# psiRP, psiRVR), checked piece by piece with explicit shifts and axis orders
+
+def _pair(x, y, z, xi=0.1):
+    return I.vortex_ring_pair_periodised(x, y, z, 0.5 * math.pi, math.pi, xi)
+
+
+def test_ring_pair_cores_and_windings():
+    """The pair psi_VR(z - d/2) psi_VR*(z + d/2) (R = pi/2, d = pi) vanishes on its two core circles
+    r = R at z = pi + d/2 and z = pi - d/2, and its phase winds by +1 around the first and by -1
+    around the second (the conjugate); the mirror images, nonzero there, change neither."""
+    R, d, xi = 0.5 * math.pi, math.pi, 0.1
+    t = np.linspace(0.0, 2.0 * math.pi, 129)
+    for zc, wind in ((math.pi + 0.5 * d, 1.0), (math.pi - 0.5 * d, -1.0)):
+        for phi in (0.0, 1.1, 2.5):                   # three points of each core circle
+            cx, cy = math.pi + R * math.cos(phi), math.pi + R * math.sin(phi)
+            assert abs(_pair(np.array(cx), np.array(cy), np.array(zc))) < 1e-12
+            eps = 0.3 * xi                             # loop in the (r, z) half-plane
+            rr = R + eps * np.cos(t)
+            ph = np.angle(_pair(math.pi + rr * math.cos(phi), math.pi + rr * math.sin(phi), zc + eps * np.sin(t)))
+            w = np.sum(np.angle(np.exp(1j * np.diff(ph)))) / (2.0 * math.pi)
+            assert abs(w - wind) < 1e-9, (zc, phi, w)
+    # between the rings and far from them there is no core
+    assert abs(_pair(np.array(math.pi), np.array(math.pi), np.array(math.pi))) > 0.5
+
+
+def test_ring_pair_mirror_images_are_paired_about_the_faces():
+    """With the images at -x and 2L - x (L = 2 pi) in each direction the periodised pair keeps the
+    pair's reflection symmetry x -> 2 pi - x in every coordinate (the conjugated image at -x maps
+    onto the one at 4 pi - x), so its values on opposite faces agree; one image alone, or images
+    at -x and 2L + x, break it.  The normal derivative is not continuous across the faces: the
+    field is only approximately periodic."""
+    rng = np.random.default_rng(0)
+    x, y, z = rng.uniform(0.0, 2.0 * math.pi, (3, 400))
+    f = _pair(x, y, z)
+    L2 = 2.0 * math.pi
+    assert np.max(np.abs(_pair(L2 - x, y, z) - f)) < 1e-13
+    assert np.max(np.abs(_pair(x, L2 - y, z) - f)) < 1e-13
+    assert np.max(np.abs(_pair(x, y, L2 - z) - f)) < 1e-13
+    zero = np.zeros_like(y)
+    assert np.max(np.abs(_pair(zero, y, z) - _pair(zero + L2, y, z))) < 1e-13
+    assert np.max(np.abs(_pair(y, z, zero) - _pair(y, z, zero + L2))) < 1e-13
+    # a mistake in the image pairing is visible
+    R, d, xi = 0.5 * math.pi, math.pi, 0.1
+    g = lambda a, b, c: I.vortex_ring_pair(a, b, c, R, d, xi)
+    wrong = lambda a, b, c: _pair(a, b, c) * np.conj(g(2 * 2 * math.pi - a, b, c)) / np.conj(g(2 * 2 * math.pi + a, b, c))
+    assert np.max(np.abs(wrong(L2 - x, y, z) - wrong(x, y, z))) > 1e-3
+
+
+def test_rvr_pade_whole_cell_shift_is_a_roll():
+    """A translation by an even number of cells in each direction is an exact roll of the pair
+    (moved(x) = base(x + X)); the Nyquist-zeroed shift phase is then the exact one."""
+    n, xi = 16, 0.2
+    dx = 2.0 * math.pi / n
+    base = I.rvr_pade_from(n, xi, [(0.0, 0.0, 0.0)], [0])
+    moved = I.rvr_pade_from(n, xi, [(2 * dx, 4 * dx, 6 * dx)], [0])
+    assert np.max(np.abs(moved - np.roll(base, (-6, -4, -2), axis=(0, 1, 2)))) < 1e-10
+    pts = I.grid_points(n)
+    direct = _pair(pts[..., 0], pts[..., 1], pts[..., 2], xi)
+    assert np.max(np.abs(base - direct)) < 1e-12
+
+
+def test_rvr_pade_axis_orders_are_transposes():
+    """psiRVR's six orders psi(x_s0, x_s1, x_s2): order s is the transpose of the identity-ordered
+    field that sends the field's axis c to the coordinate s_c -- one transpose matches, and the
+    rings, perpendicular to the pair's own z, end up perpendicular to coordinate s_2."""
+    n, xi = 16, 0.2
+    dx = 2.0 * math.pi / n
+    X = (2 * dx, 4 * dx, 6 * dx)                     # breaks the pair's x <-> y symmetry
+    ident = I.rvr_pade_from(n, xi, [X], [0])
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    for o, s in enumerate(I.AXIS_ORDERS):
+        f = I.rvr_pade_from(n, xi, [X], [o])
+        hits = [A for A in perms if np.max(np.abs(f - np.transpose(ident, A))) < 1e-12]
+        assert len(hits) == 1, (s, hits)
+        A = hits[0]
+        # array axis 2 - c holds coordinate c; the field's coordinate c comes from s_c
+        for c in range(3):
+            assert A[2 - s[c]] == 2 - c, (s, A)
+        # a core point of the first ring: pair coordinates (pi + R, pi, pi + d/2) before the shift
+        q = [0, 0, 0]
+        for c, v in enumerate((math.pi + 0.5 * math.pi, math.pi, 1.5 * math.pi)):
+            q[s[c]] = int(round((v - X[c]) / dx)) % n   # grid index along coordinate s_c
+        assert abs(f[q[2], q[1], q[0]]) < 1e-10, s
+
+
+def test_rvr_pade_is_the_product_of_its_pairs():
+    n, xi = 16, 0.2
+    shifts, orders = [(0.3, 1.7, 4.1), (5.0, 2.2, 0.9)], [4, 1]
+    both = I.rvr_pade_from(n, xi, shifts, orders)
+    one = I.rvr_pade_from(n, xi, shifts[:1], orders[:1])
+    two = I.rvr_pade_from(n, xi, shifts[1:], orders[1:])
+    assert np.max(np.abs(both - one * two)) < 1e-13
+    s, o = I.rvr_pade_draws(7, 3)
+    assert np.max(np.abs(I.rvr_pade(n, 7, xi, 3) - I.rvr_pade_from(n, xi, s, o))) == 0.0
+    assert all(0.0 <= v < 2.0 * math.pi for X in s for v in X) and all(0 <= v < 6 for v in o)
