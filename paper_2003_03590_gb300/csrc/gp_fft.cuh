@@ -158,7 +158,7 @@ __device__ __forceinline__ double2 unit_rotate(double2 v, double c, double s) { 
 
 
 // ---------------------------------------------------------------- butterflies
-// In-register DFTs of size 2, 3, 4, 8, 16, natural order in and out.
+// In-register DFTs of size 2, 3, 4, 8, 16, 32, natural order in and out.
 template <bool INV, typename V> __device__ __forceinline__ void dft2(V& a, V& b) {
   V t = a;
   a = cadd(t, b);
@@ -243,12 +243,74 @@ template <bool INV, typename V> __device__ __forceinline__ void dft16(V* v) {
   for (int i = 0; i < 16; ++i) v[i] = t[i];
 }
 
+// cos(k pi / 16), k = 0..8, and cos / sin of any multiple of pi / 16 by symmetry
+constexpr double COS_PI16[9] = {1.0,
+                                0.98078528040323044913,
+                                0.92387953251128675613,
+                                0.83146961230254523708,
+                                0.70710678118654752440,
+                                0.55557023301960222474,
+                                0.38268343236508977173,
+                                0.19509032201612826785,
+                                0.0};
+__host__ __device__ constexpr double cos_pi16(int e) {
+  e = ((e % 32) + 32) % 32;
+  return e <= 8 ? COS_PI16[e] : (e <= 16 ? -COS_PI16[16 - e] : (e <= 24 ? -COS_PI16[e - 16] : COS_PI16[32 - e]));
+}
+__host__ __device__ constexpr double sin_pi16(int e) { return cos_pi16(8 - e); }
+
+// a * w32^EXP (forward, w32 = exp(-2 pi i / 32)) or a * conj(w32^EXP) (inverse)
+template <bool INV, int EXP, typename V> __device__ __forceinline__ V rot32(V a) {
+  constexpr int e = EXP % 32;
+  if constexpr (e == 0) return a;
+  else if constexpr (e == 8) return mul_mi<INV>(a);
+  else if constexpr (e == 16) return cneg(a);
+  else if constexpr (e == 24) return mul_mi<!INV>(a);
+  else if constexpr (e == 4) return rot45<INV>(a);
+  else if constexpr (e == 12) return rot135<INV>(a);
+  else {
+    constexpr KConst c = kconst(cos_pi16(e)), s = kconst(sin_pi16(e));
+    return rotk<INV>(a, c, s);
+  }
+}
+
+// 32 = 8 x 4: DFT8 over the four stride-4 subsequences, twiddles w32^(n2 k1), DFT4 over n2:
+//   X[k1 + 8 k2] = sum_n2 w4^(n2 k2) w32^(n2 k1) sum_n1 w8^(n1 k1) x[4 n1 + n2]
+template <bool INV, typename V> __device__ __forceinline__ void dft32(V* v) {
+  V y[32];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    V u[8];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) u[n1] = v[4 * n1 + n2];
+    dft8<INV>(u);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) y[4 * k1 + n2] = u[k1];
+  }
+  // y[4 k1 + n2] = Y[n2][k1]; multiply by w32^(n2 k1)
+  y[5] = rot32<INV, 1>(y[5]);   y[6] = rot32<INV, 2>(y[6]);   y[7] = rot32<INV, 3>(y[7]);
+  y[9] = rot32<INV, 2>(y[9]);   y[10] = rot32<INV, 4>(y[10]); y[11] = rot32<INV, 6>(y[11]);
+  y[13] = rot32<INV, 3>(y[13]); y[14] = rot32<INV, 6>(y[14]); y[15] = rot32<INV, 9>(y[15]);
+  y[17] = rot32<INV, 4>(y[17]); y[18] = rot32<INV, 8>(y[18]); y[19] = rot32<INV, 12>(y[19]);
+  y[21] = rot32<INV, 5>(y[21]); y[22] = rot32<INV, 10>(y[22]); y[23] = rot32<INV, 15>(y[23]);
+  y[25] = rot32<INV, 6>(y[25]); y[26] = rot32<INV, 12>(y[26]); y[27] = rot32<INV, 18>(y[27]);
+  y[29] = rot32<INV, 7>(y[29]); y[30] = rot32<INV, 14>(y[30]); y[31] = rot32<INV, 21>(y[31]);
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1) dft4<INV>(y[4 * k1], y[4 * k1 + 1], y[4 * k1 + 2], y[4 * k1 + 3]);
+  // y[4 k1 + k2] = X[k1 + 8 k2]: natural order
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 8 * k2] = y[4 * k1 + k2];
+}
+
 template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V* v) {
   if constexpr (R == 2) dft2<INV>(v[0], v[1]);
   else if constexpr (R == 3) dft3<INV>(v[0], v[1], v[2]);
   else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
   else if constexpr (R == 8) dft8<INV>(v);
   else if constexpr (R == 16) dft16<INV>(v);
+  else if constexpr (R == 32) dft32<INV>(v);
   else static_assert(R == 2, "unsupported radix");
 }
 
@@ -266,8 +328,8 @@ template <> struct Plan<96>   { static constexpr int NP = 3, E = 24, R0 = 8,  R1
 template <> struct Plan<128>  { static constexpr int NP = 2, E = 16, R0 = 16, R1 = 8,  R2 = 1; };
 template <> struct Plan<192>  { static constexpr int NP = 3, E = 24, R0 = 8,  R1 = 8,  R2 = 3; };
 template <> struct Plan<256>  { static constexpr int NP = 2, E = 16, R0 = 16, R1 = 16, R2 = 1; };
-template <> struct Plan<512>  { static constexpr int NP = 3, E = 16, R0 = 16, R1 = 16, R2 = 2; };
-template <> struct Plan<1024> { static constexpr int NP = 3, E = 16, R0 = 16, R1 = 16, R2 = 4; };
+template <> struct Plan<512>  { static constexpr int NP = 2, E = 32, R0 = 16, R1 = 32, R2 = 1; };
+template <> struct Plan<1024> { static constexpr int NP = 2, E = 32, R0 = 32, R1 = 32, R2 = 1; };
 
 template <int L> __host__ __device__ constexpr int radix_fwd(int i) {
   return i == 0 ? Plan<L>::R0 : (i == 1 ? Plan<L>::R1 : Plan<L>::R2);
