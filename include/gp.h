@@ -230,7 +230,7 @@ long long gp_launch_count(const gp_plan* plan);
  * the tuner times the candidates on a scratch field (allocated and freed here) and keeps the
  * fastest: 0 the TMA-pipelined persistent kernel at full occupancy, 1 the same with one CTA per
  * SM, 2 the non-persistent kernel, 3 (y, z and op 7) the TMA kernel with two shared-memory
- * stages; for op 7, 0 = the fused kernel, 1 = the fused kernel with one CTA per SM (fewer planes
+ * stages, 4 (lengths >= 512, not op 7) the TMA kernel with two compute groups per CTA; for op 7, 0 = the fused kernel, 1 = the fused kernel with one CTA per SM (fewer planes
  * in flight between its phases), 3 = the fused kernel with two stages, 2 = the three
  * separate sweeps with their own variants.  cache_path (NULL: none) names a JSON file of earlier
  * choices keyed by GPU name, length, axis and op; cached choices are reused without timing and

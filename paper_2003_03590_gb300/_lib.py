@@ -12,7 +12,7 @@ GP_FP32, GP_FP64 = 0, 1
 GP_SPLIT_NKN, GP_SPLIT_KNK = 0, 1
 # sweep kinds (axis, op) and kernel variants of gp_plan_sweep_variant / gp_plan_set_sweep_variant
 OP_FWD, OP_INV, OP_INV_N_FWD, OP_N_FWD, OP_INV_N, OP_FWD_K_INV, OP_PLANE = 1, 2, 3, 4, 5, 6, 7
-VARIANT_TMA, VARIANT_TMA_ONE, VARIANT_PLAIN, VARIANT_TMA_2STAGE = 0, 1, 2, 3
+VARIANT_TMA, VARIANT_TMA_ONE, VARIANT_PLAIN, VARIANT_TMA_2STAGE, VARIANT_TMA_GROUPS = 0, 1, 2, 3, 4
 GP_FLOW_NONE, GP_FLOW_TG, GP_FLOW_ABC = 0, 1, 2
 SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 512, 1024)
 

@@ -448,6 +448,9 @@ extern "C" gp_status gp_diagnostics_noalloc(int n, double alpha, double beta, co
     return GP_ERR_INVALID_ARG;
   const int nb = (int)std::floor(std::sqrt(3.0) * n / 2.0 + 0.5) + 1;
   if (spectra && nbins < nb) return GP_ERR_INVALID_ARG;
+  // an error left pending by the caller's earlier work is reported, not consumed: the caller
+  // still reads it with cudaGetLastError
+  if (cudaPeekAtLastError() != cudaSuccess) return GP_ERR_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ERR_CUDA;
   NoAllocDevice& D = g_na_dev[dev];
@@ -471,23 +474,32 @@ extern "C" gp_status gp_diagnostics_noalloc(int n, double alpha, double beta, co
   cpx<float>* w2 = w1 + npts;
   cpx<float>* w3 = w2 + npts;
   const unsigned g = rgrid(npts);
+  if ((long long)g > NOALLOC_MAX_BLOCKS) return GP_ERR_UNSUPPORTED_SIZE;   // before any device work
   if (cudaMemsetAsync(D.acc, 0, DIAG_ACC * sizeof(double), s) != cudaSuccess) return GP_ERR_CUDA;
   if (cudaMemsetAsync(D.flag, 0, sizeof(int), s) != cudaSuccess) return GP_ERR_CUDA;
   if (cudaMemsetAsync(D.spec, 0, (size_t)4 * nb * sizeof(double), s) != cudaSuccess) return GP_ERR_CUDA;
-  if ((long long)g > NOALLOC_MAX_BLOCKS) return GP_ERR_UNSUPPORTED_SIZE;
   double* part = D.part;
+  // every launch is checked at once (an error is then this call's own: a pending error of
+  // earlier work was refused on entry)
   k_phys1<float><<<g, 256, 0, s>>>(x, npts, part, D.flag);
+  if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
   k_reduce<<<1, 256, 0, s>>>(part, (int)g, 2, D.acc);
+  if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
   if (cudaMemcpyAsync(w0, x, (size_t)npts * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return GP_ERR_CUDA;
   if (fft3<float>(F, w0, false, s) != cudaSuccess) return GP_ERR_CUDA;
   k_kspace1<float><<<g, 256, 0, s>>>(w0, w1, w2, w3, n, part + 2 * g);
+  if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
   k_reduce<<<1, 256, 0, s>>>(part + 2 * g, (int)g, 4, D.acc + 2);
+  if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
   if (fft3<float>(F, w1, true, s) != cudaSuccess || fft3<float>(F, w2, true, s) != cudaSuccess ||
       fft3<float>(F, w3, true, s) != cudaSuccess)
     return GP_ERR_CUDA;
   k_phys2<float><<<g, 256, 0, s>>>(x, w0, w1, w2, w3, npts, alpha, part + 6 * g, part + 8 * g);
+  if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
   k_reduce<<<1, 256, 0, s>>>(part + 6 * g, (int)g, 2, D.acc + 6);
+  if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
   k_reduce_max<<<1, 256, 0, s>>>(part + 8 * g, (int)g, D.acc + 8);
+  if (cudaGetLastError() != cudaSuccess) return GP_ERR_CUDA;
   for (cpx<float>* w : {w0, w1, w2, w3})
     if (fft3<float>(F, w, false, s) != cudaSuccess) return GP_ERR_CUDA;
   k_kspace2<float><<<g, 256, (size_t)4 * nb * sizeof(double), s>>>(w0, w1, w2, w3, n, nb, alpha, beta, D.spec);

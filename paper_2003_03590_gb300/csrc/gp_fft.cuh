@@ -429,11 +429,13 @@ template <int L, bool INV> __device__ __forceinline__ int out_pos(int e, int t) 
 // Uses shared memory for the exchanges between passes (two barriers each).  WARP_X: every
 // pencil's threads lie in one warp and its exchange region is private to it, so the
 // exchanges only need warp-level barriers.
-// NB: 0 = the block barrier; otherwise named barrier 1 over the first NB threads (kernels
-// whose last warp does other work than the transforms).
+// NB: 0 = the block barrier; otherwise a named barrier over a group of NB consecutive threads,
+// barrier 1 + threadIdx.x / NB (kernels whose last warps do other work than the transforms use
+// group 0; kernels with several compute groups, one barrier per group).
+template <int NB> __device__ __forceinline__ int group_bar() { return 1 + (int)threadIdx.x / NB; }
 template <int NB> __device__ __forceinline__ void bsync() {
   if constexpr (NB == 0) __syncthreads();
-  else asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
+  else asm volatile("bar.sync %0, %1;" ::"r"(group_bar<NB>()), "n"(NB) : "memory");
 }
 template <bool WARP_X, int NB = 0> __device__ __forceinline__ void xsync() {
   if constexpr (WARP_X) __syncwarp();

@@ -21,7 +21,7 @@ GP_SIZES(GP_DECL_SWEEP)
 struct TmaSweepArgs;
 struct TmaPlaneArgs;
 #define GP_DECL_TMA(L)                                                     \
-  cudaError_t tma_sweep_##L(const TmaSweepArgs&, int, int, cudaStream_t);   \
+  cudaError_t tma_sweep_##L(const TmaSweepArgs&, int, int, int, cudaStream_t);   \
   cudaError_t tma_plane_##L(TmaPlaneArgs&, int, int, cudaStream_t);
 GP_TMA_SIZES(GP_DECL_TMA)
 #undef GP_DECL_TMA
@@ -29,7 +29,8 @@ bool tma_supported(int n);
 // launch one TMA sweep for the fields psi[0..count) of length n (float32 fused path)
 cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* status, cudaStream_t s,
                       int ctas_req = 0,    // CTAs per SM; 0: as many as fit
-                      int stages = 3);     // shared-memory stages of the y/z kernels: 3 or 2
+                      int stages = 3,      // shared-memory stages of the y/z kernels: 3 or 2
+                      int groups = 1);     // compute groups per CTA: 1, or 2 (lengths >= 512)
 // launch the fused plane kernel (forward y, forward x + K + inverse x, inverse y) for the
 // fields psi[0..count) of length n; sync: device ints, at least plane_sync_ints(n, count)
 cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* sync, int* status, cudaStream_t s,
@@ -126,9 +127,9 @@ template <typename T> cudaError_t launch_vjp_nonlinear(const cpx<T>* psi_in, cpx
                                                        double shift, cudaStream_t s);
 
 // sweep variants (gp_step.cu): 0 TMA persistent, 1 TMA one CTA per SM, 2 plain, 3 TMA with two
-// stages; for OP_PLANE 0 means the fused plane kernel, 3 the same with two stages and 2 the
-// three separate sweeps it replaces
-enum { VARIANT_TMA = 0, VARIANT_TMA_ONE = 1, VARIANT_PLAIN = 2, VARIANT_TMA_2STAGE = 3 };
+// stages, 4 TMA with two compute groups per CTA (lengths >= 512); for OP_PLANE 0 means the fused
+// plane kernel, 3 the same with two stages and 2 the three separate sweeps it replaces
+enum { VARIANT_TMA = 0, VARIANT_TMA_ONE = 1, VARIANT_PLAIN = 2, VARIANT_TMA_2STAGE = 3, VARIANT_TMA_GROUPS = 4 };
 int sweep_variant(gp_plan* p, int n, int axis, int op);
 bool plane_on(gp_plan* p, int n);
 gp_status ensure_plane_sync(gp_plan* p, size_t ints);

@@ -91,16 +91,7 @@ __device__ __forceinline__ void bulk_wait2() { asm volatile("cp.async.bulk.wait_
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// AND of a predicate over the first NB threads (named barrier 1)
-template <int NB> __device__ __forceinline__ bool bar_and(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-      : "=r"(r)
-      : "r"((uint32_t)v), "n"(NB)
-      : "memory");
-  return r != 0;
-}
+
 
 // Item order.  Blocks of Q items (one phase of one plane) are ordered by "group" g: group g
 // holds phase 0 of plane g, phase 1 of plane g - D and phase 2 of plane g - 2D (those that

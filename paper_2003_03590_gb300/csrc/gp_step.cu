@@ -76,6 +76,7 @@ cudaError_t launch_sweep_variant(gp_plan* p, int n, const SweepArgs<float>& a, v
   }
   if (variant == VARIANT_PLAIN) return sweep(n, a, s);
   if (variant == VARIANT_TMA_2STAGE && a.axis != 0) return tma_sweep(n, a, psi, p->flag + 1, s, 0, 2);
+  if (variant == VARIANT_TMA_GROUPS) return tma_sweep(n, a, psi, p->flag + 1, s, 0, 3, 2);
   return tma_sweep(n, a, psi, p->flag + 1, s, variant == VARIANT_TMA_ONE ? 1 : 0);
 }
 
@@ -170,7 +171,8 @@ gp_status launch_item(gp_plan* p, const Group& G, const Item& it, void* const* p
     const bool tma = sweep_variant(p, G.n, it.axis, it.op) != VARIANT_PLAIN;
     std::string name = it.op == OP_PLANE ? std::string("k_tma_plane<") + std::to_string(G.n) + ">:y_fwd_x_fwd_k_inv_y_inv:xy"
                        : std::string(tma ? (it.axis == 0 ? "k_tma_contig<" : "k_tma_strided<")
-                                         : (it.axis == 0 ? "k_sweep_contig<float," : "k_sweep_strided<float,")) +
+                                         : G.n >= 512 ? (it.axis == 0 ? "k_sweep_contig_rc<float," : "k_sweep_strided_rc<float,")
+                                                      : (it.axis == 0 ? "k_sweep_contig<float," : "k_sweep_strided<float,")) +
                              std::to_string(G.n) + ">:" + opn[it.op] + ":" + "xyz"[it.axis];
     int kind = -1;
     for (int q = 0; q < (int)p->kinds.size(); ++q)

@@ -48,17 +48,30 @@ __device__ __forceinline__ double2 kinetic_apply(double2 x, double2 e_other, dou
 
 template <typename V> __device__ __forceinline__ V kscale(V x, KConst k) { return V{kmul(x.x, k), kmul(x.y, k)}; }
 
-// pencils per CTA
+// pencils per CTA (16: rows of 128 bytes, the fewest rows per byte read of a z-pencil tile, whose
+// rows lie one z-plane apart; float64 at 1024: 8, for the registers)
 template <typename T, int L> __host__ __device__ constexpr int strided_batch() {
-  return (L % 16 == 0) ? (L >= 1024 ? 8 : 16) : (L % 8 == 0 ? 8 : 4);
+  return (L % 16 == 0) ? ((sizeof(T) == 8 && L >= 1024) ? 8 : 16) : (L % 8 == 0 ? 8 : 4);
 }
+// float32 kernels whose threads hold 32 elements each (L >= 512) run with register caps for
+// several CTAs per SM (see rcap_blocks); their x-row CTAs have 128 threads, four per SM
+template <typename T, int L> __host__ __device__ constexpr bool rcapped() { return sizeof(T) == 4 && Plan<L>::E >= 32; }
 template <typename T, int L> __host__ __device__ constexpr int contig_batch() {
-  int b = 256 / (L / Plan<L>::E);
+  int b = (rcapped<T, L>() ? 128 : 256) / (L / Plan<L>::E);
   b = b > 64 ? 64 : (b < 1 ? 1 : b);
   while ((L * L) % b) b /= 2;
   return b;
 }
 template <int L> __host__ __device__ constexpr int contig_pitch() { return L + (L >= 16 ? L / 16 : 1); }
+// CTAs per SM the registers of the capped one-tile-per-CTA kernels must allow (y/z: 256 threads,
+// two per SM, or at 1024 512 threads, one; x: 128 threads, four per SM).  Without a cap the compiler keeps all of a thread's 32
+// loads in flight at once and uses so many registers (~175) that one 8-warp CTA fills the SM
+// (measured at 512^3: z N-forward 752 us uncapped, 452 us capped).  Kernels of shorter lengths keep
+// the compiler's own choice (naming a minimum of one CTA per SM lifts its default limit and made
+// the 256-point kernels twice as slow).
+template <typename T, int L> __host__ __device__ constexpr int rcap_blocks(bool contig) {
+  return contig ? 4 : (strided_batch<T, L>() * (L / Plan<L>::E) >= 512 ? 1 : 2);
+}
 
 struct LayStrided {  // [pos][pencil]
   int B;
@@ -87,6 +100,16 @@ __device__ __forceinline__ void sincos_m1_small(float x, float* s, float* cm1) {
 // the shrink a (cos - 1) after it would round the shrink away whenever it is below half an ulp
 // of the component -- with the same sign at every step at points where |a|^2 stays near the
 // shift, a steady gain of mass (emulated: 1.1e-8 per step at ||a|^2 - 1| = 4e-3).
+// The large-phase branch (|phase| > 1/2, i.e. ||a|^2 - shift| > 1/(2 coef): rare) is kept out of
+// line.  Inlined at every element of a thread's unrolled pencil data it would repeat sincosf's
+// argument reduction dozens of times in the kernel, and the instruction fetch of the common
+// small-phase path would then miss in the instruction cache.
+static __device__ __noinline__ float2 nonlinear_large(float2 a, float ph) {
+  float sn, cs;
+  sincosf(ph, &sn, &cs);
+  return unit_rotate(a, cs, -sn);
+}
+
 template <typename V, typename S> __device__ __forceinline__ V nonlinear(V a, S coef, S shift) {
   S r2;
   if constexpr (sizeof(S) == 4) r2 = fmaf(a.x, a.x, a.y * a.y);   // explicit: see rotk
@@ -101,8 +124,7 @@ template <typename V, typename S> __device__ __forceinline__ V nonlinear(V a, S 
       const float ui = fmaf(-a.x, sn, __fmul_rn(a.y, cm1));
       return V{__fadd_rn(a.x, ur), __fadd_rn(a.y, ui)};
     }
-    sincosf(ph, &sn, &cs);
-    return unit_rotate(a, cs, -sn);
+    return nonlinear_large(a, ph);
   } else {
     sincos(ph, &sn, &cs);
     return V{a.x * cs + a.y * sn, a.y * cs - a.x * sn};
@@ -185,27 +207,33 @@ __device__ __forceinline__ void sweep_op_body(const SweepArgs<T>& a, int t, int 
 // y or z pencils: a CTA owns B consecutive x of one (z) or (y) line.  One kernel per
 // operation: a kernel holds only the code it runs (smaller than one with every operation
 // behind a run-time switch, which missed in the instruction cache).
-template <typename T, int L, int OP>
-__global__ void __launch_bounds__(strided_batch<T, L>() * (L / Plan<L>::E))
-    k_sweep_strided(SweepArgs<T> a) {
+template <typename T, int L, int OP> __device__ __forceinline__ void strided_tile(const SweepArgs<T>& a) {
   using V = cpx<T>;
   constexpr int B = strided_batch<T, L>();
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int p = threadIdx.x % B, t = threadIdx.x / B;
-  const int x0 = (blockIdx.x % (L / B)) * B;
-  const int c = blockIdx.x / (L / B);
   const long st = (a.axis == 1) ? (long)L : (long)L * L;    // stride along the pencil
   const long sc = (a.axis == 1) ? (long)L * L : (long)L;    // stride of the other coordinate
+  const int x0 = (blockIdx.x % (L / B)) * B;
+  const int c = blockIdx.x / (L / B);
   V* base = a.psi[blockIdx.y] + x0 + p + (long)c * sc;
   auto addr = [&](int pos) { return base + (long)pos * st; };
   LayStrided lay{B};
   sweep_op_body<OP, T, L, B>(a, t, p, sm, lay, addr, x0 + p, c);
 }
+template <typename T, int L, int OP>
+__global__ void __launch_bounds__(strided_batch<T, L>() * (L / Plan<L>::E)) k_sweep_strided(SweepArgs<T> a) {
+  strided_tile<T, L, OP>(a);
+}
+template <typename T, int L, int OP>
+__global__ void __launch_bounds__(strided_batch<T, L>() * (L / Plan<L>::E), rcap_blocks<T, L>(false))
+    k_sweep_strided_rc(SweepArgs<T> a) {
+  strided_tile<T, L, OP>(a);
+}
 
 // x rows: a CTA owns B consecutive rows (y, z).
-template <typename T, int L, int OP>
-__global__ void __launch_bounds__(contig_batch<T, L>() * (L / Plan<L>::E)) k_sweep_contig(SweepArgs<T> a) {
+template <typename T, int L, int OP> __device__ __forceinline__ void contig_tile(const SweepArgs<T>& a) {
   using V = cpx<T>;
   constexpr int TP = L / Plan<L>::E;
   constexpr int B = contig_batch<T, L>();
@@ -219,6 +247,15 @@ __global__ void __launch_bounds__(contig_batch<T, L>() * (L / Plan<L>::E)) k_swe
   sweep_op_body<OP, T, L, B, LayContig<L>, decltype(addr), false, (TP <= 32)>(a, t, p, sm, lay, addr,
                                                                               (int)(row % L), (int)(row / L));
 }
+template <typename T, int L, int OP>
+__global__ void __launch_bounds__(contig_batch<T, L>() * (L / Plan<L>::E)) k_sweep_contig(SweepArgs<T> a) {
+  contig_tile<T, L, OP>(a);
+}
+template <typename T, int L, int OP>
+__global__ void __launch_bounds__(contig_batch<T, L>() * (L / Plan<L>::E), rcap_blocks<T, L>(true))
+    k_sweep_contig_rc(SweepArgs<T> a) {
+  contig_tile<T, L, OP>(a);
+}
 
 // Operations each axis supports: y/z pencils every operation but FWD_K_INV; x rows forward,
 // inverse and forward-K-inverse.  Anything else is an invalid launch.
@@ -229,6 +266,7 @@ template <typename T, int L> struct SweepLaunch {
   static constexpr int TP = L / Plan<L>::E;
   static constexpr int BS = strided_batch<T, L>();
   static constexpr int BC = contig_batch<T, L>();
+  static constexpr bool RC = rcapped<T, L>();
   static size_t smem_strided() { return sizeof(cpx<T>) * (size_t)L * BS; }
   static size_t smem_contig() { return sizeof(cpx<T>) * (size_t)contig_pitch<L>() * BC; }
   // the shared-memory limit of every operation's kernel, set together on the first launch of
@@ -237,10 +275,12 @@ template <typename T, int L> struct SweepLaunch {
     static bool done = false;
     if (done) return;
     const size_t sc = smem_contig(), ss = smem_strided();
-#define GP_ATTR_C(OPV)                                                                                  \
-  if (sc > 48 * 1024) cudaFuncSetAttribute(k_sweep_contig<T, L, OPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
-#define GP_ATTR_S(OPV)                                                                                  \
-  if (ss > 48 * 1024) cudaFuncSetAttribute(k_sweep_strided<T, L, OPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+#define GP_ATTR_C(OPV)                                                                                        \
+  if constexpr (RC) cudaFuncSetAttribute(k_sweep_contig_rc<T, L, OPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc); \
+  else if (sc > 48 * 1024) cudaFuncSetAttribute(k_sweep_contig<T, L, OPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sc);
+#define GP_ATTR_S(OPV)                                                                                        \
+  if constexpr (RC) cudaFuncSetAttribute(k_sweep_strided_rc<T, L, OPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss); \
+  else if (ss > 48 * 1024) cudaFuncSetAttribute(k_sweep_strided<T, L, OPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     GP_CONTIG_OPS(GP_ATTR_C)
     GP_STRIDED_OPS(GP_ATTR_S)
 #undef GP_ATTR_C
@@ -251,14 +291,18 @@ template <typename T, int L> struct SweepLaunch {
     const size_t sm = smem_contig();
     set_attributes();
     const long rows = (long)L * L;
-    k_sweep_contig<T, L, OP><<<dim3((unsigned)(rows / BC), (unsigned)a.count), BC * TP, sm, s>>>(a);
+    const dim3 grid((unsigned)(rows / BC), (unsigned)a.count);
+    if constexpr (RC) k_sweep_contig_rc<T, L, OP><<<grid, BC * TP, sm, s>>>(a);
+    else k_sweep_contig<T, L, OP><<<grid, BC * TP, sm, s>>>(a);
     return cudaGetLastError();
   }
   template <int OP> static cudaError_t strided(const SweepArgs<T>& a, cudaStream_t s) {
     const size_t sm = smem_strided();
     set_attributes();
     const long tiles = (long)(L / BS) * L;
-    k_sweep_strided<T, L, OP><<<dim3((unsigned)tiles, (unsigned)a.count), BS * TP, sm, s>>>(a);
+    const dim3 grid((unsigned)tiles, (unsigned)a.count);
+    if constexpr (RC) k_sweep_strided_rc<T, L, OP><<<grid, BS * TP, sm, s>>>(a);
+    else k_sweep_strided<T, L, OP><<<grid, BS * TP, sm, s>>>(a);
     return cudaGetLastError();
   }
   static cudaError_t launch(const SweepArgs<T>& a, cudaStream_t s) {

@@ -37,7 +37,7 @@ template <int L> static void box_of(int axis, cuuint32_t box[3]) {
   } else if (axis == 1) {
     box[0] = TmaStrided<L>::B; box[1] = TmaStrided<L>::BOX; box[2] = 1;
   } else {
-    box[0] = TmaStrided<L>::B; box[1] = 1; box[2] = TmaStrided<L>::BOX;
+    box[0] = TmaStrided<L, 3, z_wide<L>()>::B; box[1] = 1; box[2] = TmaStrided<L>::BOX;
   }
 }
 
@@ -68,9 +68,11 @@ static bool make_map(CUtensorMap* m, void* base, int n, int axis) {
 }
 
 cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* status, cudaStream_t s,
-                      int ctas_req, int stages) {
+                      int ctas_req, int stages, int groups) {
   if (a.axis == 0) stages = 3;
-  static TmaSweepArgs t;   // large: keep it off the stack (launches copy it)
+  // large: kept off the stack (a launch copies it); one per host thread, so plans stepped from
+  // several threads never share an argument block between its set-up and its launch
+  static thread_local TmaSweepArgs t;
   std::memset(&t, 0, sizeof(t));
   t.count = a.count;
   for (int f = 0; f < a.count; ++f)
@@ -86,7 +88,7 @@ cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* s
   t.scale_inv = a.scale_inv;
   t.status = status;
   switch (n) {
-#define GP_CASE(L) case L: return tma_sweep_##L(t, ctas_req, stages, s);
+#define GP_CASE(L) case L: return tma_sweep_##L(t, ctas_req, stages, groups, s);
     GP_TMA_SIZES(GP_CASE)
 #undef GP_CASE
     default:
@@ -98,7 +100,7 @@ cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* s
 // every z-plane of the fields psi[0..count) in one launch
 cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* sync, int* status, cudaStream_t s,
                       int stages, int skip, int ctas_per_sm) {
-  static TmaPlaneArgs t;   // large: keep it off the stack (launches copy it)
+  static thread_local TmaPlaneArgs t;   // as in tma_sweep: one per host thread
   std::memset(&t, 0, sizeof(t));
   t.count = a.count;
   cuuint32_t by[3], bx[3];

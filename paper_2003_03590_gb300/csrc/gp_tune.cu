@@ -10,6 +10,7 @@
 // and keeps the fastest; the fused plane kernel (op 7) is timed against the three sweeps it
 // replaces.  Choices are cached in a small JSON file keyed by the GPU's name.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -24,9 +25,10 @@ static std::string cache_key(const char* gpu, int n, int axis, int op) {
 
 // candidates per kind: 0-2 everywhere, 3 (two stages) for y, z and the plane kernel; the plane
 // kernel has no one-CTA variant
-static bool variant_ok(int axis, int op, int v) {
+static bool variant_ok(int axis, int op, int v, int n) {
   if (op == OP_PLANE) return v == VARIANT_TMA || v == VARIANT_TMA_ONE || v == VARIANT_PLAIN || v == VARIANT_TMA_2STAGE;
   if (v == VARIANT_TMA_2STAGE) return axis != 0;
+  if (v == VARIANT_TMA_GROUPS) return n >= 512;
   return v >= 0 && v <= 2;
 }
 
@@ -50,6 +52,7 @@ extern "C" gp_status gp_plan_autotune(gp_plan* p, const char* cache_path) {
   GP_CUDA(p, cudaGetDeviceProperties(&prop, dev));
   for (char* c = prop.name; *c; ++c)
     if (*c == '"' || *c == '|') *c = '_';
+  const bool verbose = std::getenv("GP_TUNE_VERBOSE") != nullptr;   // per-candidate times on stderr
   std::string text;
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "r")) {
@@ -81,7 +84,7 @@ extern "C" gp_status gp_plan_autotune(gp_plan* p, const char* cache_path) {
       const int axis = kind[0], op = kind[1];
       const long long key = (long long)F.n * 64 + axis * 8 + op;
       int best = -1;
-      if (!cache_lookup(text, cache_key(prop.name, F.n, axis, op), &best) || !variant_ok(axis, op, best)) {
+      if (!cache_lookup(text, cache_key(prop.name, F.n, axis, op), &best) || !variant_ok(axis, op, best, F.n)) {
         best = 0;
         if (!scratch) {
           GP_CUDA(p, cudaMalloc(&scratch, (size_t)F.npts * 8));
@@ -107,8 +110,8 @@ extern "C" gp_status gp_plan_autotune(gp_plan* p, const char* cache_path) {
           if (st != GP_OK) return st;
         }
         float best_ms = 1e30f;
-        for (int var = 0; var < 4; ++var) {
-          if (!variant_ok(axis, op, var)) continue;
+        for (int var = 0; var < 5; ++var) {
+          if (!variant_ok(axis, op, var, F.n)) continue;
           auto run = [&]() -> cudaError_t { return launch_sweep_variant(p, F.n, a, &scratch, var, p->stream); };
           for (int w = 0; w < 2; ++w) GP_CUDA(p, run());
           GP_CUDA(p, cudaEventRecord(e0, p->stream));
@@ -117,6 +120,7 @@ extern "C" gp_status gp_plan_autotune(gp_plan* p, const char* cache_path) {
           GP_CUDA(p, cudaEventSynchronize(e1));
           float ms = 0.f;
           GP_CUDA(p, cudaEventElapsedTime(&ms, e0, e1));
+          if (verbose) std::fprintf(stderr, "gp_plan_autotune: n %d axis %d op %d variant %d: %.2f us\n", F.n, axis, op, var, ms * 200.f);
           if (ms < best_ms) {
             best_ms = ms;
             best = var;
@@ -180,7 +184,7 @@ extern "C" gp_status gp_plan_set_sweep_variant(gp_plan* p, int n, int axis, int 
   if (!p) return GP_ERR_INVALID_ARG;
   const bool kind_ok = (axis == 2 && op >= OP_FWD && op <= OP_INV_N) || (axis == 1 && (op == OP_FWD || op == OP_INV)) ||
                        (axis == 0 && op == OP_FWD_K_INV) || (axis == 1 && op == OP_PLANE);
-  if (!kind_ok || !variant_ok(axis, op, variant))
+  if (!kind_ok || !variant_ok(axis, op, variant, n))
     return fail(p, GP_ERR_INVALID_ARG, "gp_plan_set_sweep_variant: unknown sweep kind or variant");
   if (p->stream) GP_CUDA(p, cudaStreamSynchronize(p->stream));
   const long long key = (long long)n * 64 + axis * 8 + op;

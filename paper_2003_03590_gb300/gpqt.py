@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import (DIAG_NAMES, GP_FLOW_ABC, GP_FLOW_NONE, GP_FLOW_TG, GP_FP32, GP_FP64, GP_SPLIT_KNK, GP_SPLIT_NKN,
                    OP_PLANE, SUPPORTED_N, VARIANT_PLAIN,
-                   VARIANT_TMA, VARIANT_TMA_2STAGE, VARIANT_TMA_ONE, Diag, FieldParams,
+                   VARIANT_TMA, VARIANT_TMA_2STAGE, VARIANT_TMA_GROUPS, VARIANT_TMA_ONE, Diag, FieldParams,
                    GPError)
 
 

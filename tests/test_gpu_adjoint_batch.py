@@ -119,6 +119,24 @@ def test_batched_ragged_plan_matches_single_plans_bitwise():
         assert torch.equal(psis[i], singles[i]), i
 
 
+def test_batched_ragged_ensemble_against_the_oracle():
+    """The configuration-4 size classes (64^3, 96^3 with radix-3 passes, 128^3, two fields each,
+    xi = 1.5 dx, dt = 0.004, SRP starts made by the oracle) advanced together by one plan: one
+    step and three steps of every field match the oracle to 1e-5 per step."""
+    dt = 0.004
+    sizes = [64, 64, 96, 96, 128, 128]
+    batch = Plan([field_params(n, dt, xi_over_dx=1.5) for n in sizes])
+    starts = [OI.srp_spectral(n, 40 + i, 4.0).astype(np.complex64).astype(np.complex128) for i, n in enumerate(sizes)]
+    for steps in (1, 3):
+        psis = [to_gpu(x, np.complex64) for x in starts]
+        batch.step(psis, steps)
+        batch.sync()
+        for i, n in enumerate(sizes):
+            p = OS.params_from_dx_ratio(n, 1.5, dt)
+            ref = OS.evolve(starts[i], p, steps)
+            assert rel_l2(to_np(psis[i]), ref) < 1e-5 * steps, (n, i, steps)
+
+
 @pytest.mark.parametrize("split", [GP_SPLIT_NKN, GP_SPLIT_KNK])
 def test_fused_plane_kernel_matches_separate_sweeps_bitwise(split):
     """The fused plane kernel (forward y, x with K, inverse y of every z-plane in one launch,
@@ -215,6 +233,35 @@ def test_fused_plane_kernel_large_lengths_bitwise(n):
     fused.sync()
     sep.sync()
     assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("n", [512, 1024])
+def test_every_sweep_variant_bitwise_at_large_lengths(n):
+    """Every kernel variant of every sweep kind of the step (TMA pipelined, one CTA per SM, plain
+    one-tile-per-CTA with register caps, two stages, two compute groups per CTA, wide z tiles at 512)
+    runs the same arithmetic: two steps agree bitwise with the default kernels."""
+    from paper_2003_03590_gb300.gpqt import VARIANT_TMA_GROUPS
+    dt = 0.001
+    kinds = [(2, 4), (2, 3), (2, 5), (2, 1), (2, 2), (1, 1), (1, 2), (0, 6)]
+    g = torch.Generator(device="cuda").manual_seed(n + 1)
+    re = torch.rand((n, n, n), device="cuda", generator=g, dtype=torch.float32)
+    im = torch.rand((n, n, n), device="cuda", generator=g, dtype=torch.float32)
+    x0 = torch.complex(re - 0.5, im - 0.5)
+    del re, im
+    ref = x0.clone()
+    Plan(field_params(n, dt, xi_over_dx=1.5)).step([ref], 2)
+    for v in (VARIANT_TMA_ONE, VARIANT_PLAIN, VARIANT_TMA_2STAGE, VARIANT_TMA_GROUPS):
+        plan = Plan(field_params(n, dt, xi_over_dx=1.5)).set_sweep_variant(n, 1, OP_PLANE, VARIANT_PLAIN)
+        for a, o in kinds:
+            if v == VARIANT_TMA_2STAGE and a == 0:
+                continue
+            plan.set_sweep_variant(n, a, o, v)
+        x = x0.clone()
+        plan.step([x], 2)
+        plan.sync()
+        assert torch.equal(x, ref), v
+        del plan, x
+    torch.cuda.empty_cache()
 
 
 def test_host_buffer_step_matches_device_step():
