@@ -198,11 +198,12 @@ def job_throughput(points_per_rank, steps, world, ms_max):
 
 
 def tuned_choices(plan, n):
-    names = {0: "tma", 1: "tma_1cta", 2: "plain", 3: "tma_2stage"}
+    names = {0: "tma", 1: "tma_1cta", 2: "plain", 3: "tma_2stage", 4: "tma_2groups"}
     kinds = {"z:n_fwd": (2, 4), "z:inv_n_fwd": (2, 3), "z:inv_n": (2, 5), "y:fwd": (1, 1), "y:inv": (1, 2),
              "x:fwd_k_inv": (0, 6)}
     out = {k: names.get(plan.sweep_variant(n, a, o), "?") for k, (a, o) in kinds.items()}
-    out["y_x_y"] = "fused plane kernel" if plan.sweep_variant(n, 1, 7) == 0 else "three sweeps"
+    pv = plan.sweep_variant(n, 1, 7)
+    out["y_x_y"] = "three sweeps" if pv == 2 else "fused plane kernel (" + names.get(pv, "?") + ")"
     return out
 
 
@@ -228,25 +229,41 @@ def time_steps(plan, psi, k):
     return e0.elapsed_time(e1)
 
 
+# Algorithmic arithmetic of one sweep kind, per grid point: 1D transforms (5 log2 N flops each, the
+# radix-2 count of an N-point complex FFT) and pointwise complex factors (6 flops: the complex
+# multiply by exp(-i phase) of N(s) or K(s)).
+SWEEP_WORK = {"fwd": (1, 0), "inv": (1, 0), "n_fwd": (1, 1), "inv_n": (1, 1), "inv_n_fwd": (2, 1),
+              "fwd_k_inv": (2, 1), "y_fwd_x_fwd_k_inv_y_inv": (4, 1)}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 (FMA) x max SM clock: 80.5
+
+
 def roofline_of(gq, plan, psi, n, ksteps, peak):
     gq.profile(plan, True)
     plan.step([psi], ksteps)
     rec = gq.profile_read(plan)
     gq.profile(plan, False)
     per_kernel = {}
+    flops_of = {}
     for name, (cnt, ms) in rec.items():
-        kern = name.split(":")[0]
+        kern, op = name.split(":")[0], name.split(":")[1]
         c, m = per_kernel.get(kern, (0, 0.0))
         per_kernel[kern] = (c + cnt, m + ms)
+        tr, pw = SWEEP_WORK.get(op, (1, 0))
+        flops_of[kern] = flops_of.get(kern, 0.0) + cnt * (tr * 5 * math.log2(n) + 6 * pw) * n ** 3
     total = sum(m for _, m in per_kernel.values())
     kern, (cnt, ms) = max(per_kernel.items(), key=lambda kv: kv[1][1])
     per_launch_s = ms / cnt / 1e3
     alg_bytes = 16.0 * n ** 3
     achieved = alg_bytes / per_launch_s / 1e9
     traffic = ncu_traffic(kern, n)
+    alg_flops = flops_of[kern] / cnt
+    tflops = alg_flops / per_launch_s / 1e12
     return {"kernel": kern, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_bytes": alg_bytes,
             "launches": cnt, "mean_launch_us": round(per_launch_s * 1e6, 2), "time_share": round(ms / total, 3),
+            "alu": {"achieved": round(tflops, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                    "frac": round(tflops / FP32_PEAK_TFLOPS, 4), "algorithmic_flops": alg_flops,
+                    "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
             "kernels": {k: {"launches": c, "ms": round(m, 3), "share": round(m / total, 3)}
                         for k, (c, m) in per_kernel.items()},
             "kinds_mean_us": {k: round(ms_ / c_ * 1e3, 2) for k, (c_, ms_) in rec.items()}}
@@ -290,17 +307,18 @@ def ensemble_leg(gq, steps=500):
             "sequential": {"value": pts * steps / (ms_s / 1e3), "ms": ms_s}, "speedup": ms_s / ms_b}
 
 
-def adjoint_leg(gq, n=128, steps=400, every=20):
+def adjoint_leg(gq, n=128, steps=400, every=20, dt=0.002):
     """Gradient of E_kin^i(psi_T) with respect to the initial phase (128^3, 400 steps, checkpoints
-    every 20) through the autograd function, float32 and float64, and their agreement."""
+    every 20, dt = 0.002: outside the split step's instability band on this grid) through the
+    autograd function, float32 and float64, and their agreement."""
     import torch
 
     from inputs import smooth_phase
     th = torch.from_numpy(smooth_phase(n, 0))
-    out = {}
+    out = {"dt": dt}
     grads = {}
     for name, prec, rdt in (("fp32", gq.GP_FP32, torch.float32), ("fp64", gq.GP_FP64, torch.float64)):
-        plan = gq.Plan(gq.field_params(n, 0.004, xi_over_dx=1.5, precision=prec))
+        plan = gq.Plan(gq.field_params(n, dt, xi_over_dx=1.5, precision=prec))
         t = th.to(rdt).cuda().requires_grad_(True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -310,7 +328,7 @@ def adjoint_leg(gq, n=128, steps=400, every=20):
         out[name] = {"seconds": time.perf_counter() - t0, "J": float(J.detach())}
         grads[name] = t.grad.double()
     # sensitivity of the float64 gradient itself to the float32 rounding of the start
-    plan = gq.Plan(gq.field_params(n, 0.004, xi_over_dx=1.5, precision=gq.GP_FP64))
+    plan = gq.Plan(gq.field_params(n, dt, xi_over_dx=1.5, precision=gq.GP_FP64))
     t = th.to(torch.float32).to(torch.float64).cuda().requires_grad_(True)
     J = gq.IncompressibleKineticEnergy.apply(gq.GPEvolve.apply(t, plan, steps, every), plan, 1e-6)
     J.backward()
@@ -319,6 +337,25 @@ def adjoint_leg(gq, n=128, steps=400, every=20):
     rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
     out["grad_rel_err_fp32_vs_fp64"] = rel(g32, g64)
     out["grad_rel_err_fp64_rounded_start_vs_fp64"] = rel(g64r, g64)
+    # the adjoint's own error: both adjoints along the float32 trajectory (its checkpoints and final
+    # state, upcast for float64), so the flow's sensitivity to the start does not enter
+    p32 = gq.Plan(gq.field_params(n, dt, xi_over_dx=1.5, precision=gq.GP_FP32))
+    p64 = gq.Plan(gq.field_params(n, dt, xi_over_dx=1.5, precision=gq.GP_FP64))
+    t32 = th.to(torch.float32).cuda()
+    psi0 = p32.psi_from_phase(0, t32)
+    psi = psi0.clone()
+    ck = []
+    for _ in range(steps // every):
+        ck.append(psi.clone())
+        p32.step([psi], every)
+    lam32, _ = p32.ekin_i_grad(0, psi, 1e-6)
+    lam64, _ = p64.ekin_i_grad(0, psi.to(torch.complex128), 1e-6)
+    for c in reversed(ck):
+        p32.adjoint_step(0, c, lam32, every)
+        p64.adjoint_step(0, c.to(torch.complex128), lam64, every)
+    gs32 = p32.phase_grad(0, psi0, lam32).double()
+    gs64 = p64.phase_grad(0, p64.psi_from_phase(0, t32.double()), lam64)
+    out["grad_rel_err_fp32_vs_fp64_same_trajectory"] = rel(gs32, gs64)
     return out
 
 
@@ -484,22 +521,64 @@ def cpu_oracle_baseline(n, dt, steps):
     return n ** 3 * steps / dt_s, dt_s
 
 
+def _oracle_step_worker(job):
+    """One float64 oracle step of the n^3 workload in a worker process (spawned: no CUDA state)."""
+    import time as _t
+    n, dt, seed = job
+    from inputs import random_psi
+    from oracle import scheme as OS
+    p = OS.params_from_dx_ratio(n, 1.5, dt)
+    psi = random_psi(n, seed, amp_jitter=0.1)
+    t0 = _t.perf_counter()
+    OS.step_nkn(psi, p)
+    return _t.perf_counter() - t0
+
+
+def host_cores():
+    """Cores of this host: os.cpu_count() and the lscpu model line."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def cpu_oracle_all_cores(n, dt, workers=None):
+    """The oracle on every host core at once: one independent float64 step of the n^3 workload per
+    core (replicas: the numpy oracle is single-threaded), throughput = workers n^3 / wall time."""
+    import multiprocessing as mp
+    workers = workers or (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_step_worker, [(8, dt, 0)] * workers)      # start-up of every worker
+        t0 = time.perf_counter()
+        per = pool.map(_oracle_step_worker, [(n, dt, w) for w in range(workers)])
+        wall = time.perf_counter() - t0
+    return workers * n ** 3 / wall, wall, max(per), workers
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and rank != 0:
         return 0
-    k = max(1, min(args.steps, 2))
+    k = 1
     w = min(args.warmup, 0)
-    val, secs = cpu_oracle_baseline(N_MAIN, DT_MAIN, k)
-    cores = 1
+    ncpu, model = host_cores()
+    val, secs, worst, cores = cpu_oracle_all_cores(N_MAIN, DT_MAIN)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": k, "warmup": w, "ms_per_step": secs * 1e3 / k, "higher_is_better": True,
+            "steps": k, "warmup": w, "ms_per_step": secs * 1e3 / cores, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"GP split step {N_MAIN}^3, xi=1.5dx, dt={DT_MAIN}, RVR {RINGS} rings",
                        "global_batch": 1, "seq_len": N_MAIN ** 3, "parallelism": "single process, host"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{k} full float64 NKN step(s) of the {N_MAIN}^3 field (numpy oracle)"},
+                             "host": {"nproc": ncpu, "lscpu_model": model},
+                             "sample": f"one full float64 NKN step of the {N_MAIN}^3 field on each of {cores} cores "
+                                       f"at once (numpy oracle, one process per core, {secs:.1f} s wall)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -555,11 +634,22 @@ def main():
         return 0
     ms_step = ms / K
     floor_frac = 32.0 * n ** 3 / (ms_step / 1e3) / (peak * 1e9)
+    # a timed region of at least a second (the driver's K may be a few ms), with the clocks sampled
+    # through it and the step time scaled by the median SM clock (clock-independent work measure)
+    k_long = max(K, int(math.ceil(1.2 / (ms_step / 1e3))))
+    clocks_l = ClockSampler(local)
+    clocks_l.start()
+    time.sleep(0.2)
+    ms_long = max_over_ranks(time_steps(plan, psi, k_long), world)
+    clk_l = clocks_l.stop()
+    long_run = {"steps": k_long, "seconds": round(ms_long / 1e3, 3), "ms_per_step": ms_long / k_long,
+                "value": job_throughput(n ** 3, k_long, world, ms_long), "clocks": clk_l,
+                "ms_per_step_x_sm_mhz": (ms_long / k_long * clk_l["sm_mhz"]) if clk_l.get("sm_mhz") else None}
 
     roof = roofline_of(gq, plan, psi, n, min(K, 200), peak)
     roof["floor_frac"] = round(floor_frac, 4)
     roof["peak_source"] = peak_src
-    roof["sweeps_per_step"] = 2 if plan.sweep_variant(n, 1, 7) == 0 else 4   # HBM passes of the field
+    roof["sweeps_per_step"] = 4 if plan.sweep_variant(n, 1, 7) == 2 else 2   # HBM passes of the field
 
     # end to end through the public C ABI with host buffers
     host = torch.empty((n, n, n), dtype=torch.complex64).pin_memory()
@@ -587,7 +677,7 @@ def main():
                        "global_batch": world, "seq_len": n ** 3, "parallelism": f"replicas x{world}",
                        "l2": f"field {8 * n ** 3 / 1e6:.0f} MB > 129 MB L2; no flush between steps",
                        "tuned": tuned_choices(plan, n)},
-            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "long_run": long_run}
 
     if not args.no_extras and rank == 0:
         extras = {}
@@ -637,7 +727,21 @@ def main():
             r = roofline_of(gq, ps, f, s, min(ks, 20), peak)
             sizes[str(s)] = {"value": s ** 3 * ks / (mss / 1e3), "ms_per_step": mss / ks, "steps": ks,
                              "floor_frac": round(32.0 * s ** 3 / (mss / ks / 1e3) / (peak * 1e9), 4),
+                             "sweeps_per_step": 4 if ps.sweep_variant(s, 1, 7) == 2 else 2,
+                             "tuned": tuned_choices(ps, s), "kinds_mean_us": r["kinds_mean_us"],
                              "dominant": {k: r[k] for k in ("kernel", "achieved", "frac", "time_share")}}
+            if s >= 1024:
+                # configuration 3: full diagnostics (float64 sums, four spectra) every 100 steps
+                free0 = torch.cuda.mem_get_info()[0]
+                ps.diagnostics(0, f)
+                torch.cuda.synchronize()
+                ws = free0 - torch.cuda.mem_get_info()[0]
+                t0 = time.perf_counter()
+                for _ in range(2):
+                    ps.diagnostics(0, f)
+                dms = (time.perf_counter() - t0) * 1e3 / 2
+                sizes[str(s)]["diagnostics"] = {"ms_per_call": dms, "workspace_bytes": ws,
+                                                "share_at_1_per_100_steps": dms / (dms + 100 * mss / ks)}
             del f, ps
             torch.cuda.empty_cache()
         extras["sizes"] = sizes
@@ -647,9 +751,15 @@ def main():
         extras["analysis_cost"] = analysis_leg(plan, psi)
         extras["argle_tg_128"] = argle_leg(gq)
         # the float64 oracle on the host cores: one full step of the same 256^3 workload
-        val, secs = cpu_oracle_baseline(n, DT_MAIN, 1)
-        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"1 full float64 NKN step of the {n}^3 field ({secs:.1f} s, numpy)"}
+        val1, secs1 = cpu_oracle_baseline(n, DT_MAIN, 1)
+        ncpu, model = host_cores()
+        valn, walln, _, cores = cpu_oracle_all_cores(n, DT_MAIN)
+        line["cpu_baseline"] = {"value": valn, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "host": {"nproc": ncpu, "lscpu_model": model},
+                                "sample": f"one full float64 NKN step of the {n}^3 field on each of {cores} cores at "
+                                          f"once (numpy oracle, one process per core, {walln:.1f} s wall)",
+                                "single_core": {"value": val1, "cores": 1,
+                                                "sample": f"1 full float64 NKN step of the {n}^3 field ({secs1:.1f} s)"}}
         line["extras"] = extras
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -22,7 +22,7 @@ struct TmaSweepArgs;
 struct TmaPlaneArgs;
 #define GP_DECL_TMA(L)                                                     \
   cudaError_t tma_sweep_##L(const TmaSweepArgs&, int, int, int, cudaStream_t);   \
-  cudaError_t tma_plane_##L(TmaPlaneArgs&, int, int, cudaStream_t);
+  cudaError_t tma_plane_##L(TmaPlaneArgs&, int, int, int, cudaStream_t);
 GP_TMA_SIZES(GP_DECL_TMA)
 #undef GP_DECL_TMA
 bool tma_supported(int n);
@@ -35,8 +35,9 @@ cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* s
 // fields psi[0..count) of length n; sync: device ints, at least plane_sync_ints(n, count)
 cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* sync, int* status, cudaStream_t s,
                       int stages = 3,       // shared-memory stages: 3, or 2 (twiddles through L1)
-                      int skip = 0,
-                      int ctas_per_sm = 0); // 0: as many CTAs per SM as fit; else at most that many     // leading tickets never handed out (test of the bounded waits)
+                      int skip = 0,         // leading tickets never handed out (test of the bounded waits)
+                      int ctas_per_sm = 0,  // 0: as many CTAs per SM as fit; else at most that many
+                      int groups = 1);      // compute groups per CTA: 1, or the grouped kernel (lengths >= 512)
 inline size_t plane_sync_ints(int n, int count) { return 1 + 2 * (size_t)n * (size_t)count; }
 
 bool supported_n(int n);

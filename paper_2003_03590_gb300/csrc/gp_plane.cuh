@@ -54,12 +54,14 @@ struct TmaPlaneArgs {
 };
 
 // NS: shared-memory stages, 3, or 2 with the twiddles read through L1 instead of shared memory
-// (one more CTA per SM at 256, registers capped to fit three)
-template <int L, int NS = 3> struct TmaPlane {
+// (one more CTA per SM at 256, registers capped to fit three).  NG: compute groups per CTA (1, or
+// several for the 512-point lengths, whose one group of 4 warps per tile leaves the SM short of
+// warps; one CTA per SM then, with NS = NG + 2 stages).
+template <int L, int NS = 3, int NG = 1> struct TmaPlane {
   static constexpr int B = TmaStrided<L>::B;               // pencils (columns or rows) per tile
   static constexpr int TP = L / Plan<L>::E;                // threads per pencil
-  static constexpr int NC = B * TP;                        // compute threads
-  static constexpr int NT = NC + 64;                       // + a loader warp and a storer warp
+  static constexpr int NC = B * TP;                        // compute threads of one group
+  static constexpr int NT = NG * NC + 64;                  // + a loader warp and a storer warp
   static constexpr int Q = L / B;                          // tiles per phase and plane
   static constexpr int TILE = B * L;                       // elements
   static constexpr int STAGE_C = B * contig_pitch<L>();    // rows use a padded exchange layout
@@ -70,10 +72,11 @@ template <int L, int NS = 3> struct TmaPlane {
   static constexpr int CHUNK = 2;                          // tickets taken per atomic
   static constexpr bool TWS = L <= 256 && NS == 3;
   // CTAs per SM the registers must allow (shared memory allows one at 1024)
-  static constexpr int MINB = (NS == 2 && L <= 256) ? 3 : (L >= 1024 ? 1 : 2);
+  static constexpr int MINB = NG > 1 ? 1 : ((NS == 2 && L <= 256) ? 3 : (L >= 1024 ? 1 : 2));
   static constexpr int TWF = tw_size<L, false>(), TWI = tw_size<L, true>();
   static constexpr size_t TWB = TWS ? (size_t)(TWF + TWI) * 16 : 0;
-  static constexpr size_t SMEM = (size_t)S * STAGE * 8 + 96 + 64 + TWB + 128;   // barriers, ring, twiddles, slack
+  static_assert(NS <= 8, "barrier arrays hold 8 stages");
+  static constexpr size_t SMEM = (size_t)S * STAGE * 8 + 192 + 64 + TWB + 128;   // barriers, ring and counts, twiddles, slack
 };
 
 __device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
@@ -132,19 +135,21 @@ __device__ __forceinline__ void plane_item(int ticket, int U, int D, int& ph, in
   }
 }
 
-template <int L, int NS>
-__global__ void __launch_bounds__(TmaPlane<L, NS>::NT, TmaPlane<L, NS>::MINB)
+template <int L, int NS, int NG>
+__global__ void __launch_bounds__(TmaPlane<L, NS, NG>::NT, TmaPlane<L, NS, NG>::MINB)
     k_tma_plane(const __grid_constant__ TmaPlaneArgs a) {
-  using G = TmaPlane<L, NS>;
+  using G = TmaPlane<L, NS, NG>;
   using V = float2;
   constexpr int B = G::B, S = G::S, STAGE = G::STAGE, TP = G::TP, Q = G::Q, BOX = G::BOX, NC = G::NC;
+  constexpr int NCT = NG * NC;                                             // compute threads of the CTA
   extern __shared__ __align__(128) unsigned char smraw[];
   const uint32_t base = smem_u32(smraw);
   V* buf = reinterpret_cast<V*>(smraw + (((base + 127u) & ~127u) - base));
   uint64_t* full = reinterpret_cast<uint64_t*>(buf + (size_t)S * STAGE);   // data of stage s landed
-  uint64_t* empty = full + 4;                                              // compute of stage s done
-  uint64_t* freed = full + 8;                                              // stage s stored (read)
-  int* ring = reinterpret_cast<int*>(full + 12);  // [s]: packed item of stage s, -1: no more items
+  uint64_t* empty = full + 8;                                              // compute of stage s done
+  uint64_t* freed = full + 16;                                             // stage s stored (read)
+  int* ring = reinterpret_cast<int*>(full + 24);  // [s]: packed item of stage s, -1: no more items
+  volatile int* issued = ring + 8;                // [s]: items the loader has put into stage s
   float4* tws = reinterpret_cast<float4*>(ring + 16);
   const int tid = threadIdx.x;
 
@@ -153,6 +158,7 @@ __global__ void __launch_bounds__(TmaPlane<L, NS>::NT, TmaPlane<L, NS>::MINB)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NC);
       mbar_init(&freed[s], 1);
+      issued[s] = 0;
     }
     fence_mbar_init();
   }
@@ -179,10 +185,10 @@ __global__ void __launch_bounds__(TmaPlane<L, NS>::NT, TmaPlane<L, NS>::MINB)
     }
   };
 
-  if (tid >= NC) {
-    // -------------------------------------------------------- loader (warp NC/32) and storer (warp NC/32 + 1)
-    if ((tid - NC) % 32 != 0) return;
-    const bool loader = tid == NC;
+  if (tid >= NCT) {
+    // -------------------------------------------------------- loader (warp NCT/32) and storer (warp NCT/32 + 1)
+    if ((tid - NCT) % 32 != 0) return;
+    const bool loader = tid == NCT;
     const int U = a.count * L;
     const int total = 3 * U * Q;
     const int D = a.lag;
@@ -246,18 +252,24 @@ __global__ void __launch_bounds__(TmaPlane<L, NS>::NT, TmaPlane<L, NS>::MINB)
         }
         mbar_expect_tx(&full[s], (unsigned)G::TILE * 8u);
         copy_tile(pend, s, true);
+        if constexpr (NG > 1) count_issued(issued + s);
         pend = -1;
         claim();   // the next item's ticket and count are read while this one loads
       }
       if (gave_up) atomicExch(a.status, 1);
-      // end marker: the compute warps stop at stage i % S; the storer stops after i items
-      if (i >= S) {
-        idle = 0;
-        while (!mbar_try_wait(&freed[i % S], (unsigned)(i / S - 1) & 1u))
-          if (stalled()) break;
+      // end markers at items i .. i + NG - 1, one for each compute group (each group stops at the
+      // first marker it meets); the storer stops after i items
+      for (int q = 0; q < NG; ++q) {
+        const int e = i + q;
+        if (e >= S) {
+          idle = 0;
+          while (!mbar_try_wait(&freed[e % S], (unsigned)(e / S - 1) & 1u))
+            if (stalled()) break;
+        }
+        ring[e % S] = -1;
+        if constexpr (NG > 1) count_issued(issued + e % S);
+        mbar_arrive(&full[e % S]);   // release: ring[] is visible to the waiters of full[]
       }
-      ring[i % S] = -1;
-      mbar_arrive(&full[i % S]);   // release: ring[] is visible to the waiters of full[]
       return;
     }
     // storer: store each computed stage, free it once read, count it once complete
@@ -298,18 +310,30 @@ __global__ void __launch_bounds__(TmaPlane<L, NS>::NT, TmaPlane<L, NS>::MINB)
     return;
   }
 
-  // -------------------------------------------------------------------- compute warps (NC threads)
+  // -------------------------------------------------------------------- compute warps (NG groups of NC threads)
   SweepArgs<float> sa{};
   sa.tw_fwd = G::TWS ? tws : a.tw_fwd;
   sa.tw_inv = G::TWS ? tws + G::TWF : a.tw_inv;
   sa.ekx = a.ekx;
   sa.ek2 = a.ek2;
   sa.scale_inv = 0;
-  for (int k = 0;; ++k) {
+  const int grp = tid / NC, lt = tid % NC;
+  for (int k = grp;; k += NG) {
     const int s = k % S;
-    const bool ok = mbar_wait_bounded(&full[s], (unsigned)(k / S) & 1u);
+    // several groups: the stage may still serve an earlier item of another group; wait until the
+    // loader has put this group's item into it (its k / S-th load), then for that load's phase
+    bool ok = true;
+    if constexpr (NG > 1) {
+      ok = false;
+      for (int w = 0; w < (1 << 22); ++w)
+        if (issued[s] > k / S) {
+          ok = true;
+          break;
+        }
+    }
+    ok = ok && mbar_wait_bounded(&full[s], (unsigned)(k / S) & 1u);
     if (!bar_and<NC>(ok)) {
-      if (tid == 0) atomicExch(a.status, 1);
+      if (lt == 0) atomicExch(a.status, 1);
       break;
     }
     const int it = ring[s];
@@ -317,14 +341,14 @@ __global__ void __launch_bounds__(TmaPlane<L, NS>::NT, TmaPlane<L, NS>::MINB)
     const int ph = it & 3, j = (it >> 2) & 511, z = (it >> 11) % L;
     V* sm = buf + (size_t)s * STAGE;
     if (ph == 1) {
-      const int p = tid / TP, t = tid % TP;
+      const int p = lt / TP, t = lt % TP;
       // the tile is [box k][row][x within box]
       auto addr = [&](int pos) { return sm + (pos / BOX) * (BOX * B) + p * BOX + (pos % BOX); };
       LayContig<L> lay;
       sweep_op_body<OP_FWD_K_INV, float, L, B, LayContig<L>, decltype(addr), true, (TP <= 32), G::TWS, NC>(
           sa, t, p, sm, lay, addr, j * B + p, z);
     } else {
-      const int p = tid % B, t = tid / B;
+      const int p = lt % B, t = lt / B;
       auto addr = [&](int pos) { return sm + pos * B + p; };
       LayStrided lay{B};
       if (ph == 0)
@@ -339,24 +363,31 @@ __global__ void __launch_bounds__(TmaPlane<L, NS>::NT, TmaPlane<L, NS>::MINB)
   }
 }
 
+// compute groups and stages of the grouped plane kernel: 512: three groups, five stages;
+// 1024: two groups, three stages (a 1024-point stage is 70 KB)
+template <int L> __host__ __device__ constexpr int plane_groups() { return L >= 1024 ? 2 : 3; }
+template <int L> __host__ __device__ constexpr int plane_group_stages() { return L >= 1024 ? 3 : 5; }
+
 template <int L> struct TmaPlaneLaunch {
-  template <int NS> static int occupancy() {
+  template <int NS, int NG> static int occupancy() {
     static int occ = -1;   // set on the first launch of the length, before any graph capture
     if (occ < 0) {
-      cudaFuncSetAttribute(k_tma_plane<L, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TmaPlane<L, NS>::SMEM);
+      cudaFuncSetAttribute(k_tma_plane<L, NS, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)TmaPlane<L, NS, NG>::SMEM);
       int nb = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_plane<L, NS>, TmaPlane<L, NS>::NT, TmaPlane<L, NS>::SMEM);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tma_plane<L, NS, NG>, TmaPlane<L, NS, NG>::NT,
+                                                    TmaPlane<L, NS, NG>::SMEM);
       occ = nb;
     }
     return occ;
   }
   // grid for a launch over `count` fields (the lag depends on it); cap > 0 limits the CTAs per SM
-  template <int NS> static int grid(int count, int cap) {
+  template <int NS, int NG> static int grid(int count, int cap) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int items = 3 * count * L * TmaPlane<L, NS>::Q;
-    int per = occupancy<NS>() > 0 ? occupancy<NS>() : 1;
+    const int items = 3 * count * L * TmaPlane<L, NS, NG>::Q;
+    int per = occupancy<NS, NG>() > 0 ? occupancy<NS, NG>() : 1;
     if (cap > 0 && cap < per) per = cap;
     const int g = sms * per;
     return g > items ? items : g;
@@ -366,20 +397,25 @@ template <int L> struct TmaPlaneLaunch {
   // complete by the time it is claimed (measured on GB300 at 256^3: 1x 168 us, 1.5x 154 us,
   // 2x 151 us, 3x 150 us per launch); the data between the phases of a plane (2 lag planes)
   // then still fits in L2.
-  template <int NS> static int lag(int grid) {
-    constexpr int per_plane = 3 * TmaPlane<L, NS>::Q;
-    return (2 * grid * (TmaPlane<L, NS>::S + TmaPlane<L, NS>::CHUNK + 1) + per_plane - 1) / per_plane + 1;
+  template <int NS, int NG> static int lag(int grid) {
+    constexpr int per_plane = 3 * TmaPlane<L, NS, NG>::Q;
+    return (2 * grid * (TmaPlane<L, NS, NG>::S + TmaPlane<L, NS, NG>::CHUNK + 1) + per_plane - 1) / per_plane + 1;
   }
-  template <int NS> static cudaError_t run(TmaPlaneArgs& a, int cap, cudaStream_t s) {
-    if (occupancy<NS>() < 1) return cudaErrorInvalidConfiguration;
-    const int g = grid<NS>(a.count, cap);
-    a.lag = lag<NS>(g);
-    k_tma_plane<L, NS><<<g, TmaPlane<L, NS>::NT, TmaPlane<L, NS>::SMEM, s>>>(a);
+  template <int NS, int NG> static cudaError_t run(TmaPlaneArgs& a, int cap, cudaStream_t s) {
+    if (occupancy<NS, NG>() < 1) return cudaErrorInvalidConfiguration;
+    const int g = grid<NS, NG>(a.count, cap);
+    a.lag = lag<NS, NG>(g);
+    k_tma_plane<L, NS, NG><<<g, TmaPlane<L, NS, NG>::NT, TmaPlane<L, NS, NG>::SMEM, s>>>(a);
     return cudaGetLastError();
   }
-  // stages: 2 or 3 shared-memory stages; ctas_per_sm: 0 = as many as fit, else at most that many
-  static cudaError_t launch(TmaPlaneArgs& a, int stages, int ctas_per_sm, cudaStream_t s) {
-    return stages == 2 ? run<2>(a, ctas_per_sm, s) : run<3>(a, ctas_per_sm, s);
+  // stages: 2 or 3 shared-memory stages; ctas_per_sm: 0 = as many as fit, else at most that many;
+  // groups > 1: the grouped kernel (lengths >= 512; its own group and stage counts)
+  static cudaError_t launch(TmaPlaneArgs& a, int stages, int ctas_per_sm, int groups, cudaStream_t s) {
+    if constexpr (L >= 512) {
+      if (groups > 1) return run<plane_group_stages<L>(), plane_groups<L>()>(a, ctas_per_sm, s);
+    }
+    if (groups > 1) return cudaErrorInvalidValue;
+    return stages == 2 ? run<2, 1>(a, ctas_per_sm, s) : run<3, 1>(a, ctas_per_sm, s);
   }
 };
 

@@ -99,7 +99,7 @@ cudaError_t tma_sweep(int n, const SweepArgs<float>& a, void* const* psi, int* s
 // the fused plane kernel (gp_plane.cuh): forward y, forward x + K + inverse x, inverse y of
 // every z-plane of the fields psi[0..count) in one launch
 cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* sync, int* status, cudaStream_t s,
-                      int stages, int skip, int ctas_per_sm) {
+                      int stages, int skip, int ctas_per_sm, int groups) {
   static thread_local TmaPlaneArgs t;   // as in tma_sweep: one per host thread
   std::memset(&t, 0, sizeof(t));
   t.count = a.count;
@@ -128,7 +128,7 @@ cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* s
   cudaError_t e = cudaMemsetAsync(sync, 0, plane_sync_ints(n, a.count) * sizeof(int), s);
   if (e != cudaSuccess) return e;
   switch (n) {
-#define GP_CASE(L) case L: return tma_plane_##L(t, stages, ctas_per_sm, s);
+#define GP_CASE(L) case L: return tma_plane_##L(t, stages, ctas_per_sm, groups, s);
     GP_TMA_SIZES(GP_CASE)
 #undef GP_CASE
     default:

@@ -26,7 +26,9 @@ static std::string cache_key(const char* gpu, int n, int axis, int op) {
 // candidates per kind: 0-2 everywhere, 3 (two stages) for y, z and the plane kernel; the plane
 // kernel has no one-CTA variant
 static bool variant_ok(int axis, int op, int v, int n) {
-  if (op == OP_PLANE) return v == VARIANT_TMA || v == VARIANT_TMA_ONE || v == VARIANT_PLAIN || v == VARIANT_TMA_2STAGE;
+  if (op == OP_PLANE)
+    return v == VARIANT_TMA || v == VARIANT_TMA_ONE || v == VARIANT_PLAIN || v == VARIANT_TMA_2STAGE ||
+           (v == VARIANT_TMA_GROUPS && n >= 512);
   if (v == VARIANT_TMA_2STAGE) return axis != 0;
   if (v == VARIANT_TMA_GROUPS) return n >= 512;
   return v >= 0 && v <= 2;

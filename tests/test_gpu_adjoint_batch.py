@@ -261,6 +261,14 @@ def test_every_sweep_variant_bitwise_at_large_lengths(n):
         plan.sync()
         assert torch.equal(x, ref), v
         del plan, x
+    # the fused plane kernel: TMA stages, one CTA per SM, two stages, several compute groups
+    for v in (VARIANT_TMA, VARIANT_TMA_ONE, VARIANT_TMA_2STAGE, VARIANT_TMA_GROUPS):
+        plan = Plan(field_params(n, dt, xi_over_dx=1.5)).set_sweep_variant(n, 1, OP_PLANE, v)
+        x = x0.clone()
+        plan.step([x], 2)
+        plan.sync()
+        assert torch.equal(x, ref), ("plane", v)
+        del plan, x
     torch.cuda.empty_cache()
 
 

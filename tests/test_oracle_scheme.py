@@ -169,3 +169,55 @@ def test_directional_flows_equal_3d_propagator():
     k2 = k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2
     exact = np.fft.ifftn(np.exp(-1j * p.alpha * k2 * 0.37) * np.fft.fftn(psi0))
     assert np.max(np.abs(S.kinetic_flow(psi0, p, 0.37) - exact)) < 1e-12
+
+
+@pytest.mark.parametrize("order", ["nkn", "knk"])
+def test_split_step_parametric_instability(order):
+    """Where c = cos(alpha k^2 dt) - beta dt sin(alpha k^2 dt) falls below -1 the same discrete
+    relation has no real frequency: a perturbation of the uniform state at that k grows by
+    |c| + sqrt(c^2 - 1) per step -- most, 1 + beta dt to first order, at alpha k^2 dt =
+    pi - atan(beta dt) -- although every sub-flow is unitary.  Just outside that band it stays
+    bounded."""
+    n, kk, eps, b, dt = 16, 4, 1e-9, 0.1, 2.0
+    x = 2 * np.pi * np.arange(n) / n
+    th = math.pi - math.atan(b)
+    p = S.Params(n=n, alpha=th / (kk * kk * dt), beta=b / dt, dt=dt)
+    psi = (1.0 + eps * np.cos(kk * x)).reshape(1, 1, n).astype(complex)
+    amp = []
+    for _ in range(61):
+        amp.append(abs(np.fft.fft(psi[0, 0])[kk]) / n)
+        psi = S.evolve(psi, p, 1, order)
+    c = math.cos(th) - b * math.sin(th)
+    assert c < -1.0
+    growth = abs(c) + math.sqrt(c * c - 1.0)
+    assert abs((amp[60] / amp[40]) ** (1.0 / 20) - growth) < 1e-6
+    assert amp[60] < 1e-6                          # still the linear regime
+    th2 = math.pi - 3.0 * b                        # outside the band: |c| < 1
+    p2 = S.Params(n=n, alpha=th2 / (kk * kk * dt), beta=b / dt, dt=dt)
+    psi = (1.0 + eps * np.cos(kk * x)).reshape(1, 1, n).astype(complex)
+    worst = 0.0
+    for _ in range(200):
+        psi = S.evolve(psi, p2, 1, order)
+        worst = max(worst, abs(np.fft.fft(psi[0, 0])[kk]) / n)
+    assert worst < 2.0 * eps
+
+
+def _unstable_shells(n, xi_over_dx, dt):
+    """Integer |k|^2 on the n^3 grid (up to 3 (n/2)^2) whose discrete Bogoliubov relation has
+    c < -1, for xi = xi_over_dx * dx and the paper's alpha = sqrt(2) xi, beta = 2 / alpha."""
+    p = S.params_from_dx_ratio(n, xi_over_dx, dt)
+    k2 = np.arange(3 * (n // 2) ** 2 + 1, dtype=np.float64)
+    th = p.alpha * k2 * dt
+    c = np.cos(th) - p.beta * dt * np.sin(th)
+    return k2[c < -1.0]
+
+
+def test_configured_time_steps_and_the_instability_band():
+    """The benchmark's 256^3 run (xi = 1.5 dx, dt = 0.002) has wavenumbers in the band -- in the
+    corners of the cube, |k| between 169 and 174 -- and so does the 128^3 run at dt = 0.004;
+    halving either step takes every grid wavenumber out of it."""
+    bad = _unstable_shells(256, 1.5, 0.002)
+    assert bad.size > 0 and 169.0 < math.sqrt(bad.min()) and math.sqrt(bad.max()) < 174.0
+    assert _unstable_shells(128, 1.5, 0.004).size > 0
+    assert _unstable_shells(256, 1.5, 0.001).size == 0
+    assert _unstable_shells(128, 1.5, 0.002).size == 0
