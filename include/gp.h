@@ -243,6 +243,21 @@ gp_status gp_plan_autotune(gp_plan* plan, const char* cache_path);
 int gp_plan_sweep_variant(gp_plan* plan, int n, int axis, int op);
 gp_status gp_plan_set_sweep_variant(gp_plan* plan, int n, int axis, int op, int variant);
 
+/* gp_plan_set_fused_batch: on = 1 makes gp_step advance every field of the plan in ONE persistent
+ * launch per call (no counterpart in the paper, which steps one field per run): the call's whole
+ * NKN schedule (Sec. 4.3, the merged half steps -- z with N, forward y, forward x with K and
+ * inverse x, inverse y, per step, and the closing z with N(dt/2)) is a list of tiles handed out
+ * in order from one device counter, and a tile of a field waits, bounded by about a second, until
+ * that field's previous sweep is complete.  The results are bitwise those of the per-sweep
+ * launches.  Meant for ensembles of small fields, where a sweep is too short to fill the GPU.
+ * Needs every field float32, NKN, of length 32, 64, 96 or 128, and at most 64 fields
+ * (GP_ERR_INVALID_ARG otherwise; nothing changes).  A repeated gp_step call with the same fields
+ * and step count replays one captured graph (the counters' reset and the launch).  Workspace:
+ * 1 + (4 nsteps + 1) * fields device ints, kept by the plan.  A wait that gives up sets the
+ * status word that gp_plan_sync and the synchronising calls report.  on = 0 returns to one
+ * launch per sweep and size class.  Synchronises the stream and drops captured graphs. */
+gp_status gp_plan_set_fused_batch(gp_plan* plan, int on);
+
 /* Imaginary-time preparation (Sec. 4.2) and its start fields (Sec. 5.1, 5.2).
  * External flows: GP_FLOW_NONE, GP_FLOW_TG (v = (sin x cos y cos z, -cos x sin y cos z, 0)),
  * GP_FLOW_ABC (the sum of the k = 1 and k = 2 ABC flows with amplitudes abc[0..2] = A, B, C;

@@ -56,6 +56,7 @@ SIGNATURES = {
     "gp_plan_autotune": (_I, [_P, ctypes.c_char_p]),
     "gp_plan_sweep_variant": (_I, [_P, _I, _I, _I]),
     "gp_plan_set_sweep_variant": (_I, [_P, _I, _I, _I, _I]),
+    "gp_plan_set_fused_batch": (_I, [_P, _I]),
     "gp_plan_sync": (_I, [_P]),
     "gp_init_tg": (_I, [_P, _I, _P]),
     "gp_init_abc": (_I, [_P, _I, _P, _P]),

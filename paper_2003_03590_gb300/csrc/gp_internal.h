@@ -39,6 +39,12 @@ cudaError_t tma_plane(int n, const SweepArgs<float>& a, void* const* psi, int* s
                       int ctas_per_sm = 0,  // 0: as many CTAs per SM as fit; else at most that many
                       int groups = 1);      // compute groups per CTA: 1, or the grouped kernel (lengths >= 512)
 inline size_t plane_sync_ints(int n, int count) { return 1 + 2 * (size_t)n * (size_t)count; }
+// a whole NKN run of float32 fields of small lengths in one persistent launch (gp_ensemble.cu)
+constexpr int GP_ENS_MAXF = 64;   // fields of one such launch
+bool ensemble_supported(int n);
+size_t ensemble_sync_ints(int nsteps, int nf);
+cudaError_t ensemble_run(gp_plan* p, const std::vector<int>& fields, void* const* psi, int nsteps, int* sync,
+                         cudaStream_t s);
 
 bool supported_n(int n);
 void split_hilo(double v, float* hi, float* lo);   // see gp_plan.cu
@@ -95,6 +101,7 @@ struct gp_plan {
   size_t plane_sync_ints = 0;
   int plane_skip = 0;                      // gp_plan_test_timeout: tickets the next launch skips
   bool prof = false;                       // per-launch event timing (gp_profile)
+  bool fused_batch = false;                // gp_plan_set_fused_batch: whole NKN runs in one launch
   std::vector<cudaEvent_t> ev_pool;        // recorded events, two per profiled launch
   std::vector<int> ev_kind;                // kind index of each profiled launch
   std::vector<std::string> kinds;          // names of the kinds seen

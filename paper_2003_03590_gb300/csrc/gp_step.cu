@@ -286,8 +286,82 @@ gp_status capture(gp_plan* p, const std::vector<Group>& groups,
 
 }  // namespace
 
+// A whole NKN run of every field in one persistent launch (gp_ensemble.cu), captured in a graph
+// with the counters' reset and replayed for a repeated call with the same fields and step count.
+static bool fused_batch_ok(gp_plan* p) {
+  if (!p->fused_batch || (int)p->f.size() > GP_ENS_MAXF) return false;
+  for (const auto& F : p->f)
+    if (F.fp64 || F.prm.split != GP_SPLIT_NKN || !ensemble_supported(F.n)) return false;
+  return true;
+}
+
+static gp_status fused_batch_steps(gp_plan* p, void* const* psi, int nsteps) {
+  std::vector<int> fields;
+  for (int i = 0; i < (int)p->f.size(); ++i) {
+    fields.push_back(i);
+    if (!ktable(p, i, p->f[i].prm.dt, false)) return fail(p, GP_ERR_OOM, "kinetic table allocation");
+  }
+  gp_status st = ensure_plane_sync(p, ensemble_sync_ints(nsteps, (int)fields.size()));
+  if (st != GP_OK) return st;
+  cudaStream_t s = p->stream;
+  std::vector<void*> key(psi, psi + p->f.size());
+  key.push_back(nullptr);   // marks a fused-run graph
+  if (p->prof) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GP_CUDA(p, cudaEventCreate(&e0));
+    GP_CUDA(p, cudaEventCreate(&e1));
+    p->ev_pool.push_back(e0);
+    p->ev_pool.push_back(e1);
+    const std::string name = "k_ensemble_run:nkn_run:xyz";
+    int kind = -1;
+    for (int q = 0; q < (int)p->kinds.size(); ++q)
+      if (p->kinds[q] == name) kind = q;
+    if (kind < 0) {
+      kind = (int)p->kinds.size();
+      p->kinds.push_back(name);
+    }
+    p->ev_kind.push_back(kind);
+    GP_CUDA(p, cudaEventRecord(e0, s));
+    GP_CUDA(p, ensemble_run(p, fields, psi, nsteps, p->plane_sync, s));
+    GP_CUDA(p, cudaEventRecord(e1, s));
+    p->launches += 1;
+    return GP_OK;
+  }
+  if (!(p->run_graph && p->run_key == key && p->run_steps == nsteps)) {
+    GP_CUDA(p, ensemble_run(p, fields, psi, nsteps, p->plane_sync, s));   // first call: direct (sets attributes)
+    p->launches += 1;
+    cudaStream_t cap;
+    GP_CUDA(p, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      e = ensemble_run(p, fields, psi, nsteps, p->plane_sync, cap);
+      cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+      if (e == cudaSuccess) e = e2;
+    }
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(p, e, "fused run capture");
+    }
+    cudaGraphExec_t g = nullptr;
+    e = cudaGraphInstantiate(&g, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaGraphInstantiate");
+    if (p->run_graph) cudaGraphExecDestroy(p->run_graph);
+    p->run_graph = g;
+    p->run_key = key;
+    p->run_steps = nsteps;
+    return GP_OK;
+  }
+  GP_CUDA(p, cudaGraphLaunch(p->run_graph, s));
+  p->launches += 1;
+  return GP_OK;
+}
+
 gp_status step_all(gp_plan* p, void* const* psi, int nsteps) {
   if (nsteps == 0) return GP_OK;
+  if (fused_batch_ok(p)) return fused_batch_steps(p, psi, nsteps);
   std::vector<Group> groups = make_groups(p);
   cudaStream_t s = p->stream;
   bool any32 = false;

@@ -207,41 +207,43 @@ __device__ __forceinline__ void sweep_op_body(const SweepArgs<T>& a, int t, int 
 // y or z pencils: a CTA owns B consecutive x of one (z) or (y) line.  One kernel per
 // operation: a kernel holds only the code it runs (smaller than one with every operation
 // behind a run-time switch, which missed in the instruction cache).
-template <typename T, int L, int OP> __device__ __forceinline__ void strided_tile(const SweepArgs<T>& a) {
+template <typename T, int L, int OP, int NB = 0>
+__device__ __forceinline__ void strided_tile(const SweepArgs<T>& a, long tile, cpx<T>* psi, int tid, cpx<T>* sm) {
+  // tile: B consecutive x of one (z) line for y pencils, of one (y) line for z pencils; tid: the
+  // thread within the NB (0: all) threads that share the tile and its exchange memory sm
   using V = cpx<T>;
   constexpr int B = strided_batch<T, L>();
-  extern __shared__ __align__(16) unsigned char smraw[];
-  V* sm = reinterpret_cast<V*>(smraw);
-  const int p = threadIdx.x % B, t = threadIdx.x / B;
+  const int p = tid % B, t = tid / B;
   const long st = (a.axis == 1) ? (long)L : (long)L * L;    // stride along the pencil
   const long sc = (a.axis == 1) ? (long)L * L : (long)L;    // stride of the other coordinate
-  const int x0 = (blockIdx.x % (L / B)) * B;
-  const int c = blockIdx.x / (L / B);
-  V* base = a.psi[blockIdx.y] + x0 + p + (long)c * sc;
+  const int x0 = (int)(tile % (L / B)) * B;
+  const int c = (int)(tile / (L / B));
+  V* base = psi + x0 + p + (long)c * sc;
   auto addr = [&](int pos) { return base + (long)pos * st; };
   LayStrided lay{B};
-  sweep_op_body<OP, T, L, B>(a, t, p, sm, lay, addr, x0 + p, c);
+  sweep_op_body<OP, T, L, B, LayStrided, decltype(addr), false, false, false, NB>(a, t, p, sm, lay, addr, x0 + p, c);
 }
 template <typename T, int L, int OP>
 __global__ void __launch_bounds__(strided_batch<T, L>() * (L / Plan<L>::E)) k_sweep_strided(SweepArgs<T> a) {
-  strided_tile<T, L, OP>(a);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  strided_tile<T, L, OP>(a, blockIdx.x, a.psi[blockIdx.y], threadIdx.x, reinterpret_cast<cpx<T>*>(smraw));
 }
 template <typename T, int L, int OP>
 __global__ void __launch_bounds__(strided_batch<T, L>() * (L / Plan<L>::E), rcap_blocks<T, L>(false))
     k_sweep_strided_rc(SweepArgs<T> a) {
-  strided_tile<T, L, OP>(a);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  strided_tile<T, L, OP>(a, blockIdx.x, a.psi[blockIdx.y], threadIdx.x, reinterpret_cast<cpx<T>*>(smraw));
 }
 
-// x rows: a CTA owns B consecutive rows (y, z).
-template <typename T, int L, int OP> __device__ __forceinline__ void contig_tile(const SweepArgs<T>& a) {
+// x rows: a tile is B consecutive rows (y, z); the exchanges of a row stay within one warp.
+template <typename T, int L, int OP>
+__device__ __forceinline__ void contig_tile(const SweepArgs<T>& a, long tile, cpx<T>* psi, int tid, cpx<T>* sm) {
   using V = cpx<T>;
   constexpr int TP = L / Plan<L>::E;
   constexpr int B = contig_batch<T, L>();
-  extern __shared__ __align__(16) unsigned char smraw[];
-  V* sm = reinterpret_cast<V*>(smraw);
-  const int p = threadIdx.x / TP, t = threadIdx.x % TP;
-  const long row = (long)blockIdx.x * B + p;
-  V* base = a.psi[blockIdx.y] + row * L;
+  const int p = tid / TP, t = tid % TP;
+  const long row = tile * B + p;
+  V* base = psi + row * L;
   auto addr = [&](int pos) { return base + pos; };
   LayContig<L> lay;
   sweep_op_body<OP, T, L, B, LayContig<L>, decltype(addr), false, (TP <= 32)>(a, t, p, sm, lay, addr,
@@ -249,12 +251,14 @@ template <typename T, int L, int OP> __device__ __forceinline__ void contig_tile
 }
 template <typename T, int L, int OP>
 __global__ void __launch_bounds__(contig_batch<T, L>() * (L / Plan<L>::E)) k_sweep_contig(SweepArgs<T> a) {
-  contig_tile<T, L, OP>(a);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  contig_tile<T, L, OP>(a, blockIdx.x, a.psi[blockIdx.y], threadIdx.x, reinterpret_cast<cpx<T>*>(smraw));
 }
 template <typename T, int L, int OP>
 __global__ void __launch_bounds__(contig_batch<T, L>() * (L / Plan<L>::E), rcap_blocks<T, L>(true))
     k_sweep_contig_rc(SweepArgs<T> a) {
-  contig_tile<T, L, OP>(a);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  contig_tile<T, L, OP>(a, blockIdx.x, a.psi[blockIdx.y], threadIdx.x, reinterpret_cast<cpx<T>*>(smraw));
 }
 
 // Operations each axis supports: y/z pencils every operation but FWD_K_INV; x rows forward,

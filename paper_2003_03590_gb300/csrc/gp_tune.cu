@@ -210,6 +210,32 @@ extern "C" gp_status gp_plan_set_sweep_variant(gp_plan* p, int n, int axis, int 
   return GP_OK;
 }
 
+extern "C" gp_status gp_plan_set_fused_batch(gp_plan* p, int on) {
+  if (!p) return GP_ERR_INVALID_ARG;
+  if (on != 0 && on != 1) return fail(p, GP_ERR_INVALID_ARG, "gp_plan_set_fused_batch: on must be 0 or 1");
+  if (on) {
+    if ((int)p->f.size() > GP_ENS_MAXF)
+      return fail(p, GP_ERR_INVALID_ARG, "gp_plan_set_fused_batch: more fields than one fused run holds");
+    for (const auto& F : p->f)
+      if (F.fp64 || F.prm.split != GP_SPLIT_NKN || !ensemble_supported(F.n))
+        return fail(p, GP_ERR_INVALID_ARG,
+                    "gp_plan_set_fused_batch: needs float32 NKN fields of lengths 32, 64, 96 or 128");
+  }
+  if (p->stream) GP_CUDA(p, cudaStreamSynchronize(p->stream));
+  p->fused_batch = on == 1;
+  if (p->cycle_graph) {
+    cudaGraphExecDestroy(p->cycle_graph);
+    p->cycle_graph = nullptr;
+  }
+  if (p->run_graph) {
+    cudaGraphExecDestroy(p->run_graph);
+    p->run_graph = nullptr;
+  }
+  p->run_key.clear();
+  p->last_key.clear();
+  return GP_OK;
+}
+
 extern "C" gp_status gp_plan_test_timeout(gp_plan* p, int tiles) {
   if (!p) return GP_ERR_INVALID_ARG;
   if (tiles < 0) return fail(p, GP_ERR_INVALID_ARG, "gp_plan_test_timeout: negative tile count");

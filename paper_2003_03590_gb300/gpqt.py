@@ -251,6 +251,11 @@ class Plan:
         self._check(self._lib.gp_plan_set_sweep_variant(self._h, n, axis, op, variant))
         return self
 
+    def set_fused_batch(self, on=True):
+        """Advance every field of a step call in one persistent launch (see gp.h); returns self."""
+        self._check(self._lib.gp_plan_set_fused_batch(self._h, 1 if on else 0))
+        return self
+
     def phase_grad(self, field, psi, lam):
         n = self.n(field)
         g = torch.empty((n, n, n), dtype=self.real_dtype(field), device="cuda")
