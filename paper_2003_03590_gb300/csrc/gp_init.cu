@@ -54,13 +54,24 @@ __global__ void k_srp_filter(double2* w, int n, double inv_k02) {
   }
 }
 
-__global__ void k_sum_re2(const double2* w, long long npts, double* acc) {
+// Sum of Re(w)^2 as SUM_BLOCKS partial sums, each formed in a fixed order (a thread's strided
+// elements in turn, a warp's tree, the block's warps in turn); the host adds the partials in
+// order.  The total does not depend on scheduling, so a seed always gives the same field.
+constexpr int SUM_BLOCKS = 64, SUM_THREADS = 1024;
+__global__ void __launch_bounds__(SUM_THREADS) k_sum_re2(const double2* w, long long npts, double* part) {
+  __shared__ double wsum[SUM_THREADS / 32];
   double v = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npts; i += (long long)gridDim.x * blockDim.x)
-    v += w[i].x * w[i].x;
+    v = fma(w[i].x, w[i].x, v);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(acc, v);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < SUM_THREADS / 32; ++q) t += wsum[q];
+    part[blockIdx.x] = t;
+  }
 }
 
 template <typename T> __global__ void k_phase_out(const double2* w, cpx<T>* psi, long long npts, double scale) {
@@ -300,12 +311,14 @@ template <typename T> static gp_status srp_spectral(gp_plan* p, int field, cpx<T
   k_srp_filter<<<igrid(npts), 256, 0, s>>>(w, F.n, 1.0 / (k0 * k0));
   GP_CUDA(p, cudaGetLastError());
   GP_CUDA(p, fft3<double>(F, w, true, s));
-  GP_CUDA(p, cudaMemsetAsync(p->acc, 0, sizeof(double), s));
-  k_sum_re2<<<igrid(npts), 256, 0, s>>>(w, npts, p->acc);
+  static_assert(SUM_BLOCKS <= 64, "partial sums fit the plan's accumulators");
+  k_sum_re2<<<SUM_BLOCKS, SUM_THREADS, 0, s>>>(w, npts, p->acc);
   GP_CUDA(p, cudaGetLastError());
-  double sum = 0.0;
-  GP_CUDA(p, cudaMemcpyAsync(&sum, p->acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  double part[SUM_BLOCKS];
+  GP_CUDA(p, cudaMemcpyAsync(part, p->acc, sizeof(part), cudaMemcpyDeviceToHost, s));
   GP_CUDA(p, cudaStreamSynchronize(s));
+  double sum = 0.0;
+  for (int b = 0; b < SUM_BLOCKS; ++b) sum += part[b];
   if (!(sum > 0.0)) return fail(p, GP_ERR_NONFINITE, "gp_init_srp: filtered noise has zero or non-finite RMS");
   const double scale = trms / std::sqrt(sum / (double)npts);
   k_phase_out<T><<<igrid(npts), 256, 0, s>>>(w, psi, npts, scale);

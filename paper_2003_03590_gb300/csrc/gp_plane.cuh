@@ -168,19 +168,28 @@ __global__ void __launch_bounds__(TmaPlane<L, NS, NG>::NT, TmaPlane<L, NS, NG>::
   }
   __syncthreads();
 
+  // L2 priorities: the phase-0 loads (the plane as the z sweep left it, read once here) and the
+  // phase-2 stores (the step's output) go first; the plane between its phases (stored by
+  // phases 0 and 1, read back by phases 1 and 2) stays, so that it does not round-trip to HBM
+  uint64_t pol_first = 0, pol_last = 0;
+  if (tid >= NG * NC) {
+    pol_first = l2_policy_evict_first();
+    pol_last = l2_policy_evict_last();
+  }
   auto copy_tile = [&](int it, int s, bool load) {   // TMA copy of item `it` between HBM/L2 and stage s
     const int ph = it & 3, j = (it >> 2) & 511, u = it >> 11;
     const int f = u / L, z = u - f * L;
     V* st = buf + (size_t)s * STAGE;
+    const uint64_t pol = (load ? ph == 0 : ph == 2) ? pol_first : pol_last;
 #pragma unroll
     for (int k = 0; k < G::NBOX; ++k) {
       V* sk = st + (size_t)k * BOX * B;
       if (ph == 1) {
-        if (load) tma_load_3d(sk, &a.map_x[f], &full[s], k * BOX, j * B, z);
-        else tma_store_3d(&a.map_x[f], sk, k * BOX, j * B, z);
+        if (load) tma_load_3d_hint(sk, &a.map_x[f], &full[s], k * BOX, j * B, z, pol);
+        else tma_store_3d_hint(&a.map_x[f], sk, k * BOX, j * B, z, pol);
       } else {
-        if (load) tma_load_3d(sk, &a.map_y[f], &full[s], j * B, k * BOX, z);
-        else tma_store_3d(&a.map_y[f], sk, j * B, k * BOX, z);
+        if (load) tma_load_3d_hint(sk, &a.map_y[f], &full[s], j * B, k * BOX, z, pol);
+        else tma_store_3d_hint(&a.map_y[f], sk, j * B, k * BOX, z, pol);
       }
     }
   };

@@ -131,6 +131,46 @@ template <typename V, typename S> __device__ __forceinline__ V nonlinear(V a, S 
   }
 }
 
+// N(s) on all E elements of a thread (float32 in pairs).  Two elements at a time through packed
+// FP32x2 operations whose lanes round exactly as the scalar ones of nonlinear(): the same
+// results, about half the instructions of the small-phase path.  A pair with a large phase
+// takes the scalar path for both.
+__device__ __forceinline__ float2 f2c(float c) { return float2{c, c}; }
+__device__ __forceinline__ void nonlinear_pair(float2& a, float2& b, float coef, float shift) {
+  const float2 X{a.x, b.x}, Y{a.y, b.y};
+  const float2 r2 = __ffma2_rn(X, X, __fmul2_rn(Y, Y));
+  const float2 ph = __fmul2_rn(f2c(coef), __fadd2_rn(r2, f2c(-shift)));
+  if (fabsf(ph.x) <= 0.5f && fabsf(ph.y) <= 0.5f) {
+    const float2 z = __fmul2_rn(ph, ph);
+    float2 pc = __ffma2_rn(z, f2c(-2.7557319e-7f), f2c(2.4801587e-5f));
+    pc = __ffma2_rn(z, pc, f2c(-1.3888889e-3f));
+    pc = __ffma2_rn(z, pc, f2c(4.1666668e-2f));
+    pc = __ffma2_rn(z, pc, f2c(-0.5f));
+    const float2 cm1 = __fmul2_rn(z, pc);
+    float2 ps = __ffma2_rn(z, f2c(2.7557319e-6f), f2c(-1.9841270e-4f));
+    ps = __ffma2_rn(z, ps, f2c(8.3333333e-3f));
+    ps = __ffma2_rn(z, ps, f2c(-0.16666667f));
+    const float2 sn = __ffma2_rn(__fmul2_rn(ph, z), ps, ph);
+    const float2 ur = __ffma2_rn(Y, sn, __fmul2_rn(X, cm1));
+    const float2 ui = __ffma2_rn(X, __fmul2_rn(sn, f2c(-1.0f)), __fmul2_rn(Y, cm1));
+    const float2 rx = __fadd2_rn(X, ur), ry = __fadd2_rn(Y, ui);
+    a = float2{rx.x, ry.x};
+    b = float2{rx.y, ry.y};
+  } else {
+    a = nonlinear(a, coef, shift);
+    b = nonlinear(b, coef, shift);
+  }
+}
+template <int E, typename V, typename S> __device__ __forceinline__ void nonlinear_all(V* v, S coef, S shift) {
+  if constexpr (sizeof(S) == 4 && E % 2 == 0) {
+#pragma unroll
+    for (int e = 0; e < E; e += 2) nonlinear_pair(v[e], v[e + 1], coef, shift);
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = nonlinear(v[e], coef, shift);
+  }
+}
+
 template <typename T, int L, bool INV, class GetAddr>
 __device__ __forceinline__ void load_pattern(cpx<T>* v, int t, const GetAddr& addr) {
   constexpr int E = Plan<L>::E;
@@ -162,10 +202,7 @@ __device__ __forceinline__ void sweep_op_body(const SweepArgs<T>& a, int t, int 
   V v[E];
   load_pattern<T, L, IN_INV>(v, t, addr);
   if constexpr (TILE_IN_SMEM) bsync<NB>();
-  if constexpr (OP == OP_N_FWD) {
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = nonlinear(v[e], a.nl_coef, a.nl_shift);
-  }
+  if constexpr (OP == OP_N_FWD) nonlinear_all<E>(v, a.nl_coef, a.nl_shift);
   if constexpr (OP == OP_FWD || OP == OP_N_FWD || OP == OP_FWD_K_INV)
     fft_regs<T, L, B, Lay, false, WARP_X, TW_SH, NB>(v, t, p, sm, lay, a.tw_fwd);
   if constexpr (IN_INV) {
@@ -176,8 +213,11 @@ __device__ __forceinline__ void sweep_op_body(const SweepArgs<T>& a, int t, int 
         for (int e = 0; e < E; ++e) v[e] = kscale(v[e], inv_l);
       }
     } else {
+      if (sc) {
 #pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = nonlinear(sc ? kscale(v[e], inv_l) : v[e], a.nl_coef, a.nl_shift);
+        for (int e = 0; e < E; ++e) v[e] = kscale(v[e], inv_l);
+      }
+      nonlinear_all<E>(v, a.nl_coef, a.nl_shift);
     }
   }
   if constexpr (OP == OP_INV_N_FWD) {
