@@ -199,6 +199,10 @@ __device__ __forceinline__ void sweep_op_body(const SweepArgs<T>& a, int t, int 
   constexpr bool IN_INV = OP == OP_INV || OP == OP_INV_N || OP == OP_INV_N_FWD;
   constexpr bool OUT_INV = OP == OP_INV || OP == OP_INV_N || OP == OP_FWD_K_INV;
   const bool sc = a.scale_inv != 0;
+  // the row's kinetic factor of (y, z) is read before the forward transform, so that its latency
+  // is hidden behind the transform's arithmetic
+  [[maybe_unused]] float4 eo{};
+  if constexpr (OP == OP_FWD_K_INV && sizeof(T) == 4) eo = __ldg(a.ek2 + i2 * L + i1);
   V v[E];
   load_pattern<T, L, IN_INV>(v, t, addr);
   if constexpr (TILE_IN_SMEM) bsync<NB>();
@@ -229,7 +233,6 @@ __device__ __forceinline__ void sweep_op_body(const SweepArgs<T>& a, int t, int 
       // two products by factors exact to float64 (hi + lo), each rounded once: the magnitude
       // of the field is not biased by the kinetic factor, which is the same for a given k in
       // every step
-      const float4 eo = __ldg(a.ek2 + i2 * L + i1);
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = twmul_k(twmul_k(v[e], __ldg(a.ekx + out_pos<L, false>(e, t))), eo);
     } else {
