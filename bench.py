@@ -7,10 +7,14 @@ float32 storage, fused sweeps.  A bench step is one time step of the scheme; the
 region is one gp_step call advancing K steps on a field already resident in HBM.
 
 Metric: N^3 * steps / s (grid points advanced per second), whole job.  Also reported:
-  roofline     the dominant sweep kernel: algorithmic bytes (16 B per point per launch,
-               one read and one write of the complex64 field) / its mean CUDA-event time,
-               against the measured HBM copy bandwidth; floor_frac = 32 N^3 B / (t_step * BW)
-               (two sweeps per step is the fewest a 3D FFT pair admits)
+  roofline     the dominant sweep kernel (bound "alu": the issue of its float32 arithmetic
+               limits it): algorithmic flops (5 log2 N per point and 1D transform, 6 per
+               pointwise complex factor) / its mean CUDA-event time against the nominal FP32
+               rate; beside it ("hbm") algorithmic bytes (16 B per point per launch, one read
+               and one write of the complex64 field) against the measured HBM copy bandwidth,
+               the ncu DRAM traffic and FMA-pipe / issue activity when taken on the current
+               source; floor_frac = 32 N^3 B / (t_step * BW) (two sweeps per step is the
+               fewest a 3D FFT pair admits)
   e2e          the same metric through gp_step_host with the field in pinned host memory,
                one host->device copy, one step and one device->host copy per bench step
   cpu_baseline the float64 numpy oracle, one full 256^3 step, on the host
@@ -89,6 +93,23 @@ def ncu_traffic(kernel, n):
             if len(parts) == 4 and not line.startswith("#") and parts[0] == kernel and int(parts[1]) == n \
                     and parts[3] == cur:
                 return float(parts[2])
+    return None
+
+
+def ncu_pipes(kernel, n):
+    """FMA-pipe and issue-slot activity (% of peak) of a kernel from the committed ncu summary, if
+    taken on the current kernel source (lines: <kernel> <n> <fma_pipe_pct> <issue_pct> <source_hash>)."""
+    path = os.path.join(ROOT, "profiles", "ncu_pipes.txt")
+    if not os.path.exists(path):
+        return None
+    cur = kernel_source_hash()
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) == 5 and not line.startswith("#") and parts[0] == kernel and int(parts[1]) == n \
+                    and parts[4] == cur:
+                return {"fma_pipe_active_pct": float(parts[2]), "issue_active_pct": float(parts[3]),
+                        "source": "profiles/ncu_pipes.txt"}
     return None
 
 
@@ -258,12 +279,16 @@ def roofline_of(gq, plan, psi, n, ksteps, peak):
     traffic = ncu_traffic(kern, n)
     alg_flops = flops_of[kern] / cnt
     tflops = alg_flops / per_launch_s / 1e12
-    return {"kernel": kern, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_bytes": alg_bytes,
+    # The sweep kernels are limited by the issue of their float32 arithmetic, not by HBM (ncu:
+    # DRAM well below peak, issue slots and the FMA pipe the busiest units): the bound is "alu",
+    # against the nominal FP32 rate, with the HBM figures and the ncu pipe counters beside it.
+    return {"kernel": kern, "bound": "alu", "achieved": round(tflops, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
+            "unit": "TFLOP/s", "frac": round(tflops / FP32_PEAK_TFLOPS, 4), "traffic": traffic,
+            "algorithmic_flops": alg_flops, "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+            "pipes": ncu_pipes(kern, n),
+            "hbm": {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "algorithmic_bytes": alg_bytes},
             "launches": cnt, "mean_launch_us": round(per_launch_s * 1e6, 2), "time_share": round(ms / total, 3),
-            "alu": {"achieved": round(tflops, 2), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-                    "frac": round(tflops / FP32_PEAK_TFLOPS, 4), "algorithmic_flops": alg_flops,
-                    "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
             "kernels": {k: {"launches": c, "ms": round(m, 3), "share": round(m / total, 3)}
                         for k, (c, m) in per_kernel.items()},
             "kinds_mean_us": {k: round(ms_ / c_ * 1e3, 2) for k, (c_, ms_) in rec.items()}}
@@ -664,7 +689,7 @@ def main():
 
     roof = roofline_of(gq, plan, psi, n, min(K, 200), peak)
     roof["floor_frac"] = round(floor_frac, 4)
-    roof["peak_source"] = peak_src
+    roof["hbm"]["peak_source"] = peak_src
     roof["sweeps_per_step"] = 4 if plan.sweep_variant(n, 1, 7) == 2 else 2   # HBM passes of the field
 
     # end to end through the public C ABI with host buffers
@@ -745,7 +770,8 @@ def main():
                              "floor_frac": round(32.0 * s ** 3 / (mss / ks / 1e3) / (peak * 1e9), 4),
                              "sweeps_per_step": 4 if ps.sweep_variant(s, 1, 7) == 2 else 2,
                              "tuned": tuned_choices(ps, s), "kinds_mean_us": r["kinds_mean_us"],
-                             "dominant": {k: r[k] for k in ("kernel", "achieved", "frac", "time_share")}}
+                             "dominant": {"kernel": r["kernel"], "time_share": r["time_share"],
+                                          "alu_frac": r["frac"], "hbm_frac": r["hbm"]["frac"]}}
             if s >= 1024:
                 # configuration 3: full diagnostics (float64 sums, four spectra) every 100 steps
                 free0 = torch.cuda.mem_get_info()[0]
