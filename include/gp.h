@@ -304,12 +304,13 @@ gp_status gp_argle_converge(gp_plan* plan, int field, void* psi_dev, int flow, c
 gp_status gp_plan_sync(gp_plan* plan);
 
 /* Test hook of the bounded waits (no counterpart in the paper): the next launch of the fused
- * plane kernel never hands out its first `tiles` tiles, so the tiles that depend on them wait
- * for counts that never complete.  Those waits give up after about a second, the launch ends
- * with the status word set, and the next gp_plan_sync (or gp_step_host, gp_diagnostics)
- * returns GP_ERR_TIMEOUT; the field is then invalid, the plan and the CUDA context stay
- * usable.  Applies to one launch (the step must use the fused kernel: a length with TMA
- * kernels and the default variant); captured graphs are dropped. */
+ * plane kernel (or, with gp_plan_set_fused_batch, the next fused run) never hands out its first
+ * `tiles` tiles, so the tiles that depend on them wait for counts that never complete.  Those
+ * waits give up after about a second, the launch ends with the status word set, and the next
+ * gp_plan_sync (or gp_step_host, gp_diagnostics) returns GP_ERR_TIMEOUT; the field is then
+ * invalid, the plan and the CUDA context stay usable.  Applies to one launch (the step must use
+ * the fused plane kernel -- a length with TMA kernels and the default variant -- or the fused
+ * run); captured graphs are dropped. */
 gp_status gp_plan_test_timeout(gp_plan* plan, int tiles);
 
 /* Message of the last failed call on this plan ("" if none); valid until the next call. */

@@ -45,6 +45,7 @@ struct EnsArgs {
   int ch_f0[GP_ENS_MAXF + 1];
   long long ch_t0[GP_ENS_MAXF + 1];   // first ticket of chunk c
   int steps;
+  int skip;                     // leading tickets never handed out (a test of the bounded waits)
   int* ticket;
   int* done;                    // [stage][field] items counted
   int* status;
@@ -142,13 +143,13 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ensemble_run(const __grid_co
   // thread 0 holds the CTA's next ticket while the current item runs (the atomic's latency is
   // hidden); the oldest unfinished ticket is then always an item in progress, never one held
   long long next = 0;
-  if (threadIdx.x == 0) next = (unsigned)atomicAdd(a.ticket, 1);
+  if (threadIdx.x == 0) next = (long long)(unsigned)atomicAdd(a.ticket, 1) + a.skip;
   for (;;) {
     // thread 0 takes the ticket, decodes it and waits for the item's inputs; one barrier then
     // hands (ticket, ok) to the CTA
     if (threadIdx.x == 0) {
       const long long tk = next;
-      if (next < total) next = (unsigned)atomicAdd(a.ticket, 1);
+      if (next < total) next = (long long)(unsigned)atomicAdd(a.ticket, 1) + a.skip;
       int ok = 1;
       if (tk < total) {
         int f, g, kind, step, item;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ensemble_run(const __grid_co
           const int need = pk == 2 ? a.off_c[f + 1] - a.off_c[f] : a.off_s[f + 1] - a.off_s[f];
           const int* c = a.done + (long)(g - 1) * a.nf + f;
           ok = 0;
-          for (int i = 0; i < (1 << 22); ++i) {
+          for (int i = 0; i < (1 << 20); ++i) {   // about a second
             if (ld_acquire_gpu(c) >= need) {
               ok = 1;
               break;
@@ -225,7 +226,7 @@ constexpr size_t ENS_CHUNK_BYTES = 40u << 20;
 size_t ensemble_sync_ints(int nsteps, int nf) { return 1 + (size_t)(4 * nsteps + 1) * (size_t)nf; }
 
 cudaError_t ensemble_run(gp_plan* p, const std::vector<int>& fields, void* const* psi, int nsteps, int* sync,
-                         cudaStream_t s) {
+                         cudaStream_t s, int skip) {
   static thread_local EnsArgs a;   // large: off the stack, one per host thread
   std::memset(&a, 0, sizeof(a));
   const int nf = (int)fields.size();
@@ -253,6 +254,7 @@ cudaError_t ensemble_run(gp_plan* p, const std::vector<int>& fields, void* const
   }
   a.nf = nf;
   a.steps = nsteps;
+  a.skip = skip;
   // chunks of consecutive fields
   a.nch = 0;
   a.ch_f0[0] = 0;

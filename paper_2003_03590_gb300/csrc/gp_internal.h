@@ -44,7 +44,7 @@ constexpr int GP_ENS_MAXF = 64;   // fields of one such launch
 bool ensemble_supported(int n);
 size_t ensemble_sync_ints(int nsteps, int nf);
 cudaError_t ensemble_run(gp_plan* p, const std::vector<int>& fields, void* const* psi, int nsteps, int* sync,
-                         cudaStream_t s);
+                         cudaStream_t s, int skip = 0);
 
 bool supported_n(int n);
 void split_hilo(double v, float* hi, float* lo);   // see gp_plan.cu

@@ -97,3 +97,25 @@ def test_fused_batch_rejects_what_it_cannot_run():
     p.set_fused_batch(True).step([y], 3)
     p.sync()
     assert torch.equal(x, y)
+
+
+def test_fused_run_bounded_wait_gives_up_and_reports_timeout():
+    """A fused run whose first tile is never handed out: the tiles that need it wait about a
+    second, give up, and the run ends with the status word set (GP_ERR_TIMEOUT at the next
+    check); the plan and the context stay usable and the next run is exact again."""
+    sizes = [32, 64]
+    fused, per = _pair(sizes, 0.002)
+    fa = [to_gpu(random_psi(n, 500 + i), np.complex64) for i, n in enumerate(sizes)]
+    fused.test_timeout(1)
+    fused.step(fa, 1)
+    with pytest.raises(GPError) as err:
+        fused.sync()
+    assert err.value.status == 5             # GP_ERR_TIMEOUT
+    good = [to_gpu(random_psi(n, 510 + i), np.complex64) for i, n in enumerate(sizes)]
+    ref = [g.clone() for g in good]
+    fused.step(good, 2)
+    per.step(ref, 2)
+    fused.sync()
+    per.sync()
+    for x, y in zip(good, ref):
+        assert torch.equal(x, y)
