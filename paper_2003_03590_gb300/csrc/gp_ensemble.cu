@@ -283,18 +283,22 @@ cudaError_t ensemble_run(gp_plan* p, const std::vector<int>& fields, void* const
   cudaError_t e = cudaMemsetAsync(sync, 0, ensemble_sync_ints(nsteps, nf) * sizeof(int), s);
   if (e != cudaSuccess) return e;
   // the shared-memory limit and the CTAs per SM, for the largest tile any length here may need
-  static int occ = -1;
-  static size_t occ_smem = 0;
-  size_t smax = 0;
-#define GP_ENS_CASE(L) smax = ens_smem<L>() > smax ? ens_smem<L>() : smax;
-  GP_ENS_SIZES(GP_ENS_CASE)
+  // (set once per process, thread-safely, on the first launch, which is never inside a capture)
+  static const size_t smax = [] {
+    size_t m = 0;
+#define GP_ENS_CASE(L) m = ens_smem<L>() > m ? ens_smem<L>() : m;
+    GP_ENS_SIZES(GP_ENS_CASE)
 #undef GP_ENS_CASE
-  if (occ < 0) {
-    cudaFuncSetAttribute(k_ensemble_run, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ensemble_run, ENS_THREADS, smax);
-    occ_smem = smax;
-  }
-  if (occ < 1 || smem > occ_smem) return cudaErrorInvalidConfiguration;
+    return m;
+  }();
+  static const int occ = [] {
+    int o = 0;
+    if (cudaFuncSetAttribute(k_ensemble_run, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_ensemble_run, ENS_THREADS, smax) != cudaSuccess)
+      return 0;
+    return o;
+  }();
+  if (occ < 1 || smem > smax) return cudaErrorInvalidConfiguration;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

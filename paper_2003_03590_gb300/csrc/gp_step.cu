@@ -46,6 +46,18 @@ gp_status ensure_plane_sync(gp_plan* p, size_t ints) {
     cudaFree(p->plane_sync);
     p->plane_sync = nullptr;
     p->plane_sync_ints = 0;
+    // captured graphs hold the old counters' address: drop them
+    if (p->cycle_graph) {
+      cudaGraphExecDestroy(p->cycle_graph);
+      p->cycle_graph = nullptr;
+    }
+    if (p->run_graph) {
+      cudaGraphExecDestroy(p->run_graph);
+      p->run_graph = nullptr;
+    }
+    p->cycle_key.clear();
+    p->run_key.clear();
+    p->last_key.clear();
   }
   if (cudaMalloc(&p->plane_sync, ints * sizeof(int)) != cudaSuccess) {
     p->plane_sync = nullptr;

@@ -3,7 +3,7 @@ bitwise against the per-sweep launches, and against the oracle."""
 import numpy as np
 import pytest
 
-from inputs import random_psi
+from inputs import random_direction, random_psi
 from oracle import initial as OI
 from oracle import scheme as OS
 from tests._util import rel_l2, to_gpu, to_np
@@ -119,3 +119,24 @@ def test_fused_run_bounded_wait_gives_up_and_reports_timeout():
     per.sync()
     for x, y in zip(good, ref):
         assert torch.equal(x, y)
+
+
+def test_graph_replay_after_the_counter_buffer_grows():
+    """A fused run's graph holds the address of the plan's counters.  An adjoint step (its
+    recomputation runs the fused plane kernel, whose counters are larger) reallocates them; the
+    next call must not replay the stale graph: the field still equals the per-sweep launches'."""
+    n, dt = 32, 0.002
+    fused, per = _pair([n], dt)
+    x = to_gpu(random_psi(n, 7), np.complex64)
+    y = x.clone()
+    fused.step([x], 1)
+    fused.step([x], 1)                       # replays the graph captured by the first call
+    per.step([y], 1)                         # the same calls (a 2-step call merges the half steps)
+    per.step([y], 1)
+    lam = to_gpu(random_direction(n, 8), np.complex64)
+    fused.adjoint_step(0, x.clone(), lam, 2)
+    fused.step([x], 1)
+    per.step([y], 1)
+    fused.sync()
+    per.sync()
+    assert torch.equal(x, y)
