@@ -272,6 +272,47 @@ def test_every_sweep_variant_bitwise_at_large_lengths(n):
     torch.cuda.empty_cache()
 
 
+def test_plans_stepped_from_two_host_threads():
+    """Two plans on their own streams, stepped from two host threads at once (the library's
+    per-launch argument blocks, tensor maps included, are per host thread): each field equals
+    the same steps taken alone."""
+    import threading
+    n, steps = 128, 6
+    starts = [to_gpu(random_psi(n, 90 + i), np.complex64) for i in range(2)]
+    refs = []
+    for x in starts:
+        r = x.clone()
+        Plan(field_params(n, 0.002, xi_over_dx=1.5)).step([r], steps)
+        refs.append(r)
+    torch.cuda.synchronize()
+    plans = [Plan(field_params(n, 0.002, xi_over_dx=1.5), stream=torch.cuda.Stream()) for _ in range(2)]
+    fields = [x.clone() for x in starts]
+    torch.cuda.synchronize()
+    errors = []
+
+    def run(i):
+        try:
+            for _ in range(5):   # several calls: the first ones launch directly, later ones replay graphs
+                plans[i].step([fields[i]], steps)
+                plans[i].sync()
+                fields[i].copy_(starts[i])
+                torch.cuda.current_stream().synchronize()
+            plans[i].step([fields[i]], steps)
+            plans[i].sync()
+        except Exception as e:  # noqa: BLE001 -- reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
+    assert not errors, errors
+    for x, r in zip(fields, refs):
+        assert torch.equal(x, r)
+
+
 def test_host_buffer_step_matches_device_step():
     n = 32
     plan = Plan(field_params(n, 0.004, xi_over_dx=1.5))
