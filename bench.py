@@ -348,6 +348,40 @@ def ensemble_leg(gq, steps=500):
             "fused_speedup_vs_batched": ms_b / ms_f, "fused_speedup_vs_sequential": ms_s / ms_f}
 
 
+def config3_run(gq, plan, f, steps=2000, every=100):
+    """Configuration 3 as specified: 1024^3, xi = 1.5 dx, dt = 0.001, SRP start (k0 = 8, seed
+    0), 2000 steps with the full diagnostics (float64 sums, four spectra) every 100 steps.  The
+    wall time covers steps and diagnostics (each diagnostics call synchronises).  The time step
+    puts grid wavenumbers in the split step's instability band (growth up to 1 + beta dt = 1.15
+    per step), so the run reports the step at which the energy leaves its start value by 1e-3
+    and the first non-finite field, if any: the scheme's property at this dt, float64 alike."""
+    import torch
+    f = plan.init_srp(0, f, seed=0, mode=0, p0=8.0, p1=math.pi)
+    d0, _ = plan.diagnostics(0, f)
+    e0, n0 = d0["E"], d0["N"]
+    hist, departed, nonfinite = [], None, None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in range(steps // every):
+        plan.step([f], every)
+        try:
+            d, _ = plan.diagnostics(0, f)
+            rel_e, rel_n = d["E"] / e0 - 1.0, d["N"] / n0 - 1.0
+            hist.append([(c + 1) * every, rel_e, rel_n])
+            if departed is None and abs(rel_e) > 1e-3:
+                departed = (c + 1) * every
+        except gq.GPError as e:   # a non-finite field: the band's growth has overflowed
+            if e.status != 6:
+                raise
+            nonfinite = nonfinite or (c + 1) * every
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    return {"steps": steps, "diagnostics_every": every, "seconds": secs,
+            "N3_steps_per_s_with_diagnostics": 1024 ** 3 * steps / secs,
+            "energy_departs_1e-3_at_step": departed, "first_nonfinite_at_step": nonfinite,
+            "rel_energy_and_mass_every_100": hist}
+
+
 def adjoint_leg(gq, n=128, steps=400, every=20, dt=0.002):
     """Gradient of E_kin^i(psi_T) with respect to the initial phase (128^3, 400 steps, checkpoints
     every 20, dt = 0.002: outside the split step's instability band on this grid) through the
@@ -784,6 +818,7 @@ def main():
                 dms = (time.perf_counter() - t0) * 1e3 / 2
                 sizes[str(s)]["diagnostics"] = {"ms_per_call": dms, "workspace_bytes": ws,
                                                 "share_at_1_per_100_steps": dms / (dms + 100 * mss / ks)}
+                sizes[str(s)]["configuration_3_run"] = config3_run(gq, ps, f)
             del f, ps
             torch.cuda.empty_cache()
         extras["sizes"] = sizes
