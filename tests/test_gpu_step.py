@@ -140,6 +140,16 @@ def test_large_grid_one_step(n):
     assert rel_l2(got, ref) < 1e-5
 
 
+@pytest.mark.parametrize("n", [128, 192])
+def test_white_field_one_step(n):
+    """One step of a field with every Fourier mode populated (random phase, jittered modulus) at
+    the lengths between the small grids and 256: 128 (radix 16 x 8) and 192 (three passes with a
+    radix-3 one), every butterfly and twiddle carrying data."""
+    psi0 = random_psi(n, 31, amp_jitter=0.2)
+    got, ref = _run(n, GP_FP32, GP_SPLIT_NKN, 1, psi0, dt=0.002)
+    assert rel_l2(got, ref) < 1e-5
+
+
 @pytest.mark.parametrize("n", [512, 1024])
 def test_largest_grids_plane_wave_and_linear_limit(n):
     """At 512^3 / 1024^3 (no full oracle step): plane waves are exact for the scheme, so every
