@@ -55,6 +55,28 @@ def test_configuration2_ring_field_per_step_and_three_steps():
             assert e3 < 3e-5, e3
 
 
+def test_configuration2_per_step_parity_along_the_gpu_trajectory():
+    """The same 256^3 ring field advanced by the GPU itself to steps 10, 100 and 999: from each of
+    those complex64 states (the input of both sides) one GPU step matches one oracle step to 1e-5.
+    At this time step the grid-scale modes in the split step's instability band grow along the
+    run, so the later states are far from the smooth start: every butterfly carries data."""
+    n, dt = 256, 0.002
+    p = OS.params_from_dx_ratio(n, 1.5, dt)
+    plan = Plan(field_params(n, dt, xi_over_dx=1.5, precision=GP_FP32))
+    xi = math.sqrt(p.alpha / p.beta)
+    psi = to_gpu(OI.rvr_tanh(n, 0, xi, 40, 4 * xi, 12 * xi), np.complex64)
+    done = 0
+    for k in (10, 100, 999):
+        plan.step([psi], k - done)
+        plan.sync()
+        done = k
+        state = to_np(psi)
+        ref = OS.step_nkn(state, p)
+        got = _gpu_steps(plan, state, 1)
+        e = rel_l2(got, ref)
+        assert e < 1e-5, (k, e)
+
+
 def test_512_full_oracle_step_on_a_white_phase_field():
     """One step at 512^3 from a field with |psi| = 1 +- 0.2 and a uniform random phase at every
     point: every Fourier mode is populated, so every twiddle and butterfly of the 512-point
