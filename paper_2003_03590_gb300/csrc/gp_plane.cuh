@@ -402,13 +402,13 @@ template <int L> struct TmaPlaneLaunch {
     return g > items ? items : g;
   }
   // Tickets in flight: each CTA holds up to S loaded items, the rest of a chunk and the item
-  // being claimed.  A lag of twice that many tickets (in planes) keeps an item's inputs
-  // complete by the time it is claimed (measured on GB300 at 256^3: 1x 168 us, 1.5x 154 us,
-  // 2x 151 us, 3x 150 us per launch); the data between the phases of a plane (2 lag planes)
-  // then still fits in L2.
+  // being claimed.  A lag of 1.75 times that many tickets (in planes) keeps an item's inputs
+  // complete by the time it is claimed and the data between the phases of a plane (2 lag
+  // planes) in L2 (measured on GB300 at 256^3 with the L2 hints: 1.25x 154 us, 1.5x 150 us,
+  // 1.75x 146.2 us and 301 MB of DRAM traffic, 2x 145.9 us and 365 MB, per launch).
   template <int NS, int NG> static int lag(int grid) {
     constexpr int per_plane = 3 * TmaPlane<L, NS, NG>::Q;
-    return (2 * grid * (TmaPlane<L, NS, NG>::S + TmaPlane<L, NS, NG>::CHUNK + 1) + per_plane - 1) / per_plane + 1;
+    return (7 * grid * (TmaPlane<L, NS, NG>::S + TmaPlane<L, NS, NG>::CHUNK + 1) / 4 + per_plane - 1) / per_plane + 1;
   }
   template <int NS, int NG> static cudaError_t run(TmaPlaneArgs& a, int cap, cudaStream_t s) {
     if (occupancy<NS, NG>() < 1) return cudaErrorInvalidConfiguration;
