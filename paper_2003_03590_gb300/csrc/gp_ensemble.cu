@@ -189,7 +189,9 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ensemble_run(const __grid_co
       }
     }
     __syncthreads();   // every thread's stores of the item, and the CTA's shared memory is free again
-    if (threadIdx.x == 0) {
+    // counted by a thread of the second warp, so that the fence overlaps thread 0's work on the
+    // next ticket (that work may wait for this very count: it is not blocked by it)
+    if (threadIdx.x == 32) {
       __threadfence();
       atomicAdd(a.done + (long)g * a.nf + f, 1);
     }
