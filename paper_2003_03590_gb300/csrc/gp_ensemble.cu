@@ -51,6 +51,9 @@ struct EnsArgs {
   int* status;
 };
 
+__device__ __forceinline__ void red_release_gpu_add_ens(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -189,12 +192,10 @@ __global__ void __launch_bounds__(ENS_THREADS, 2) k_ensemble_run(const __grid_co
       }
     }
     __syncthreads();   // every thread's stores of the item, and the CTA's shared memory is free again
-    // counted by a thread of the second warp, so that the fence overlaps thread 0's work on the
-    // next ticket (that work may wait for this very count: it is not blocked by it)
-    if (threadIdx.x == 32) {
-      __threadfence();
-      atomicAdd(a.done + (long)g * a.nf + f, 1);
-    }
+    // counted by a thread of the second warp with a release reduction (the barrier above orders
+    // every thread's stores before it), overlapping thread 0's work on the next ticket (that work
+    // may wait for this very count: it is not blocked by it)
+    if (threadIdx.x == 32) red_release_gpu_add_ens(a.done + (long)g * a.nf + f, 1);
   }
 }
 
